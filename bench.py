@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Throughput of the match-count top-k hot path on one GB300 (or N replicas).
+
+One step = one batch through the whole path: query compile (keyword look-up,
+count bounds), the fused postings scan + c-PQ kernel and the per-query
+top-k merge, for 1024 LSH queries against 1,000,000 objects x 256 keywords
+(k = 100).  ``value`` is queries/s with the inputs already in HBM; ``e2e``
+is the same through the C ABI from pinned host buffers with the copies
+inside the timed region.  ``--impl reference`` times the CPU oracle on a
+bounded sample of the same workload instead.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl genie|reference]
+Under torchrun (N > 1) every rank holds an index replica and runs its own
+1024 queries (weak scaling); only the timing uses a (gloo) collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "match-count top-k queries/s and posting entries/s (% HBM peak); p99 latency"
+UNIT = "queries/s"
+N_OBJECTS, N_QUERIES, K = 1_000_000, 1024, 100
+WORKLOAD = ("lsh-1m: 1,000,000 objects x 256 p-stable LSH keywords (bucket width 4, "
+            "bucket mod 8192), 1024 queries from the same 1000-component mixture, k=100")
+REF_SAMPLE = 32      # oracle queries per reference step
+BASELINE_SAMPLE = 64  # oracle queries for the cpu_baseline object
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["genie", "reference"], default="genie")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload(rank: int, world: int):
+    import synth
+    w = synth.lsh(N_OBJECTS, N_QUERIES * world, K, config=2)
+    if world > 1:
+        w = w.subset(np.arange(rank * N_QUERIES, (rank + 1) * N_QUERIES))
+    return w
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def traffic_from_profile(kernel_src: str):
+    """Per-launch DRAM bytes of the scan kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged since the capture."""
+    p = os.path.join(ROOT, "profiles", "scan_cpq_lsh1m_ncu.md")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        text = f.read()
+    m_sha = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b:
+        return None
+    with open(kernel_src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    return float(m_b.group(1)) if sha == m_sha.group(1) else None
+
+
+def cpu_baseline(w, n_sample: int) -> dict:
+    import oracle
+    sub = w.subset(np.arange(n_sample))
+    oracle.topk(sub.subset(np.arange(2)))  # load and warm
+    t0 = time.perf_counter()
+    oracle.topk(sub)
+    dt = time.perf_counter() - t0
+    return {"value": n_sample / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "first %d of the %d queries, brute force over all %d objects "
+                      "(%.1f s wall)" % (n_sample, w.n_queries, w.n_objects, dt)}
+
+
+def config_dict(w, world, entries):
+    return {"workload": WORKLOAD, "n_objects": w.n_objects, "n_queries": w.n_queries, "k": K,
+            "postings": int(w.nnz), "entries_per_step": int(entries),
+            "l2": "inputs larger than L2 (index %.2f GB vs 126 MB L2), not flushed" % (
+                (w.nnz * 4 + (w.vocab + 1) * 8 + w.vocab * 33 * 4) / 1e9),
+            "parallelism": "replicas x%d (query batches, no data-path collective)" % world}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    w = workload(0, 1)
+    sub = w.subset(np.arange(REF_SAMPLE))
+    oracle.topk(sub.subset(np.arange(2)))
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.topk(sub)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    step_s = sum(times) / len(times)
+    value = REF_SAMPLE / step_s
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "impl": "reference",
+            "config": config_dict(w, 1, 0),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(),
+                             "kind": "oracle",
+                             "sample": "%d queries per step (first %d of %d), brute force over "
+                                       "%d objects" % (REF_SAMPLE, REF_SAMPLE, w.n_queries,
+                                                       w.n_objects)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_genie(args, rank, world, local):
+    import torch
+    from paper_1603_08390_gb300 import _build, genie, runner
+
+    _build.build()
+    torch.cuda.set_device(local)
+    w = workload(rank, world)
+    idx = runner.build_index(w)
+    Q = w.n_queries
+    d_q_off, d_q_kw = runner.to_dev(w.q_off), runner.to_dev(w.q_kw)
+    out = runner.Outputs(Q, K)
+    stream = torch.cuda.current_stream()
+
+    def step(events=None):
+        qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
+        opts = genie.make_opts(scan_events=events) if events is not None else None
+        genie.genie_search(idx, qs, K, out.ids, out.counts, out.n_valid, opts=opts, stream=stream)
+        return qs
+
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    for _ in range(args.warmup):
+        qs = step()
+    torch.cuda.synchronize()
+    entries = qs.n_entries
+    del qs
+    scan_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    for b, e in scan_ev:  # materialise the events before handing them to the library
+        b.record(stream)
+        e.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    step_ev[0].record(stream)
+    for i in range(args.steps):
+        step(scan_ev[i])
+        step_ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    total_ms = step_ev[0].elapsed_time(step_ev[-1])
+    per_step = [step_ev[i].elapsed_time(step_ev[i + 1]) for i in range(args.steps)]
+    scan_ms = statistics.mean(b.elapsed_time(e) for b, e in scan_ev)
+    total_ms = max_over_ranks(total_ms, world)
+    value = Q * world * args.steps / (total_ms / 1e3)
+
+    # end to end through the C ABI from pinned host memory
+    h_q_off = torch.from_numpy(w.q_off.view(np.int32)).pin_memory()
+    h_q_kw = torch.from_numpy(w.q_kw.view(np.int32)).pin_memory()
+    h_ids = torch.empty(Q * K, dtype=torch.int32).pin_memory()
+    h_counts = torch.empty(Q * K, dtype=torch.int32).pin_memory()
+    h_nv = torch.empty(Q, dtype=torch.int32).pin_memory()
+    e_q_off = torch.empty_like(d_q_off)
+    e_q_kw = torch.empty_like(d_q_kw)
+
+    def e2e_step():
+        e_q_off.copy_(h_q_off, non_blocking=True)
+        e_q_kw.copy_(h_q_kw, non_blocking=True)
+        qs = genie.genie_make_queries(idx, e_q_off, e_q_kw, Q, stream)
+        genie.genie_search(idx, qs, K, out.ids, out.counts, out.n_valid, stream=stream)
+        h_ids.copy_(out.ids, non_blocking=True)
+        h_counts.copy_(out.counts, non_blocking=True)
+        h_nv.copy_(out.n_valid, non_blocking=True)
+
+    for _ in range(max(3, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    h2d = (Q + 1) * 4 + int(w.q_off[-1]) * 4
+    d2h = 2 * Q * K * 4 + Q * 4
+
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    algo_bytes = 4.0 * entries  # one 4-byte object id read per posting scanned
+    achieved = algo_bytes / (scan_ms / 1e3) / 1e9
+    src = os.path.join(ROOT, "paper_1603_08390_gb300", "csrc", "search.cu")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": config_dict(w, world, entries),
+        "entries_per_s": entries * world * args.steps / (total_ms / 1e3),
+        "latency_ms": {"batch_p50": float(np.percentile(per_step, 50)),
+                       "batch_p99": float(np.percentile(per_step, 99))},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic_from_profile(src),
+                     "kernel": "scan_cpq_kernel<4>", "peak_kind": peak_kind + " hbm_gbs",
+                     "scan_ms": scan_ms, "algorithmic_bytes_per_launch": algo_bytes},
+        "e2e": {"value": Q * world * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, BASELINE_SAMPLE)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_genie(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

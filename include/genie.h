@@ -1,0 +1,239 @@
+/*
+ * genie.h -- C ABI of the GB300 match-count top-k search library.
+ *
+ * The library answers batches of match-count queries (Definition 2.1, Sec.
+ * 2.1) against an inverted index resident in GPU memory (Sec. 3.2) and returns
+ * the top-k objects of every query, ranked by match count descending and then
+ * object id ascending.  Counting and top-k selection run in CUDA kernels for
+ * sm_103a through the count priority queue c-PQ (Sec. 3.3: Bitmap Counter,
+ * Hash Table, ZipperArray, AuditThreshold; Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named d_* are DEVICE pointers (cudaMalloc'd or any memory the
+ *     current device can address); h_* are HOST pointers.  Inputs are owned by
+ *     the caller and only read.  Handles (genie_index, genie_queries,
+ *     genie_server) are owned by the library and released by *_destroy.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; entry points that must read a value
+ *     back from the device (sizes, validation flags) synchronise that stream
+ *     and say so.
+ *   - Object id = row index of the object in the object CSR (uint32).
+ *     Objects are SETS of keywords (Sec. 2.1): a keyword repeated inside one
+ *     object is rejected.  Queries are MULTISETS of items: MC sums over items
+ *     (Definition 2.1), so a keyword given twice counts twice.
+ *   - Result layout: d_ids[q*k + j], d_counts[q*k + j] for rank j of query q;
+ *     ranks past the number of matching objects hold id 0xFFFFFFFF and count
+ *     0; d_n_valid[q] = min(k_q, #objects with MC >= 1).  Objects with MC = 0
+ *     are never returned.
+ *   - Every failure is reported by the returned status; no entry point traps
+ *     or aborts.  genie_last_error() gives the message of the calling thread's
+ *     last failure.
+ *   - The device must be a compute capability 10.3 GPU (sm_103a).  Calls use
+ *     the CUDA device that is current on the calling thread.
+ */
+#ifndef GENIE_H
+#define GENIE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int genie_status;
+#define GENIE_OK 0
+#define GENIE_ERR_INVALID_ARG 1   /* bad sizes, ids, ranges, k; nothing enqueued */
+#define GENIE_ERR_OUT_OF_MEMORY 2 /* a device or host allocation failed */
+#define GENIE_ERR_CUDA 3          /* a CUDA call failed (message has the CUDA error) */
+#define GENIE_ERR_CAPACITY 4      /* a fixed capacity was exceeded (server slots) */
+#define GENIE_ERR_TIMEOUT 5       /* a bounded device or host wait ran out */
+
+typedef void* genie_stream; /* cudaStream_t */
+
+typedef struct genie_index genie_index;
+typedef struct genie_queries genie_queries;
+
+/* Largest supported values (checked; larger -> GENIE_ERR_INVALID_ARG). */
+#define GENIE_MAX_K 1024u          /* results per query */
+#define GENIE_MAX_BOUND 4095u      /* count bound of one query (see genie_make_queries) */
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char* genie_last_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int genie_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Index (Sec. 3.2, List Array + Position Map; Fig. 3)                       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  uint32_t n_objects;
+  uint32_t vocab;          /* keyword ids are < vocab */
+  uint64_t nnz;            /* postings = sum of object sizes */
+  uint32_t max_object_len; /* largest object (keywords) */
+  uint32_t chunk_shift;    /* the object-range split: 2^chunk_shift ids per chunk */
+  uint32_t n_chunks;       /* ceil(n_objects / 2^chunk_shift) */
+  uint32_t reserved;
+  uint64_t device_bytes;   /* device memory held by the index */
+} genie_index_info;
+
+/*
+ * Build the inverted index on the device from objects given as keyword sets.
+ * Paper: Sec. 2.1 (objects, keywords, postings lists), Sec. 3.2 (List Array
+ * holding all postings lists, Position Map from keyword to its list), Sec.
+ * 3.2.1 (one-to-many position map of sublists).
+ *
+ *   d_obj_off  [n_objects+1] uint32, device: object o holds keywords
+ *              d_obj_kw[d_obj_off[o] .. d_obj_off[o+1]-1]; d_obj_off[0] = 0,
+ *              non-decreasing.
+ *   d_obj_kw   [nnz] uint32, device: keyword ids < vocab, distinct within an
+ *              object, any order.
+ *   n_objects  1 .. 2^31; vocab 1 .. 2^31.
+ *   chunk_shift  log2 of the object-id range of one sublist (the unit a
+ *              search block counts on chip): 12..20, or 0 for the default 15.
+ *   out        receives the index handle (library-owned; free it with
+ *              genie_index_destroy).  Unchanged on failure.
+ *
+ * The index holds: per keyword its postings list of object ids in ascending
+ * order (List Array), the list offsets (Position Map), and per keyword the
+ * positions where each chunk of 2^chunk_shift object ids starts in its list
+ * (sublist map).  The inputs are not referenced after the call.
+ * Synchronises `stream` (sizes and validation).  Errors: INVALID_ARG for
+ * malformed offsets, keyword >= vocab or a repeated keyword in an object;
+ * OUT_OF_MEMORY; CUDA.
+ */
+genie_status genie_build_index(const uint32_t* d_obj_off, const uint32_t* d_obj_kw,
+                               uint32_t n_objects, uint32_t vocab, uint32_t chunk_shift,
+                               genie_stream stream, genie_index** out);
+
+/* Release an index (NULL is ignored).  Synchronises the device. */
+void genie_index_destroy(genie_index* index);
+
+/* Sizes of an index. */
+genie_status genie_index_get_info(const genie_index* index, genie_index_info* out);
+
+/*
+ * Copy the CSR of the index out (for inspection and tests).
+ *   d_kw_off   [vocab+1] uint64, device: list of keyword v is
+ *              d_post_ids[d_kw_off[v] .. d_kw_off[v+1]-1].
+ *   d_post_ids [nnz] uint32, device: object ids, ascending within each list.
+ * Either pointer may be NULL.  Asynchronous on `stream`.
+ */
+genie_status genie_index_export(const genie_index* index, uint64_t* d_kw_off,
+                                uint32_t* d_post_ids, genie_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Query compiler (Sec. 2.1 items -> keywords; Sec. 3.2 list look-up)        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  uint32_t n_queries;
+  uint32_t max_bound;      /* largest count bound B_q over the batch */
+  uint64_t n_keywords;     /* keywords after expansion, with multiplicity */
+  uint64_t n_entries;      /* postings the batch scans: sum over queries of sum of df */
+} genie_queries_info;
+
+/*
+ * Keyword queries (LSH signatures, Sec. 4.1.1; n-gram or word sets, Sec.
+ * 5.1-5.2): each item is one keyword.
+ *   d_q_off [n_queries+1] uint32, device; d_q_kw keywords < vocab.
+ *   n_queries  1 .. 2^24.
+ * The count bound of query q is B_q = min(|Q|, max_object_len * max
+ * multiplicity of a keyword in Q); queries with B_q > GENIE_MAX_BOUND are
+ * rejected.  The handle copies what it needs; inputs are not referenced
+ * after the call.  Synchronises `stream`.  Errors: INVALID_ARG (malformed
+ * offsets, keyword >= vocab, bound too large), OUT_OF_MEMORY, CUDA.
+ */
+genie_status genie_make_queries(const genie_index* index, const uint32_t* d_q_off,
+                                const uint32_t* d_q_kw, uint32_t n_queries, genie_stream stream,
+                                genie_queries** out);
+
+/*
+ * Relational range queries (Example 2.1, Sec. 5.3).  The index must hold
+ * keyword d*values_per_dim + v for value v of attribute d (the encoded pair of
+ * Sec. 2.1).  Query q has items d_item_off[q] .. d_item_off[q+1]-1; item i is
+ * (d_dim[i], [d_lo[i], d_hi[i]]) and expands to the keywords d*values_per_dim
+ * + v for every v in [lo, hi] clipped to [0, values_per_dim).  A range that
+ * lies outside the value domain contributes nothing; lo > hi is INVALID_ARG.
+ * B_q = min(number of expanded keywords, max_object_len * items of q).
+ * Synchronises `stream`.
+ */
+genie_status genie_compile_ranges(const genie_index* index, uint32_t values_per_dim,
+                                  const uint32_t* d_item_off, const uint32_t* d_dim,
+                                  const int32_t* d_lo, const int32_t* d_hi, uint32_t n_queries,
+                                  genie_stream stream, genie_queries** out);
+
+/* Release compiled queries (NULL is ignored).  Synchronises the device. */
+void genie_queries_destroy(genie_queries* queries);
+
+genie_status genie_queries_get_info(const genie_queries* queries, genie_queries_info* out);
+
+/*
+ * Per-query facts computed by the compiler (device outputs, any may be NULL):
+ *   d_bound   [n_queries] uint32: B_q;
+ *   d_entries [n_queries] uint64: postings scanned = sum of df over its keywords;
+ *   d_features [n_queries * 64] float: the histogram features of the
+ *             k-th-count predictor (bin 0: keywords with df = 0; bin b >= 1:
+ *             keywords with floor(log2 df) = b-1, clipped to 63), each count
+ *             scaled by 1/32.
+ * Asynchronous on `stream`.
+ */
+genie_status genie_queries_export(const genie_queries* queries, uint32_t* d_bound,
+                                  uint64_t* d_entries, float* d_features, genie_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Search (Sec. 3.2 scan + Sec. 3.3 c-PQ, Algorithm 1, Theorem 3.1)          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  /* Per-query seed of the AuditThreshold (device, [n_queries] uint32, or
+   * NULL for the paper's start value 1).  A seed s_q > 1 closes the Gate below
+   * s_q; results stay exact when s_q <= the true k-th count.  With seeds the
+   * search verifies every query and reruns the ones it cannot certify with
+   * s = 1 (this synchronises `stream` once to read the rerun count). */
+  const uint32_t* d_seed;
+  /* Tuning (0 = automatic): log2 of object ids counted by one block, threads
+   * per block, hash-table slots per block (power of two). */
+  uint32_t block_shift;
+  uint32_t threads;
+  uint32_t ht_slots;
+  /* Optional diagnostics (device, NULL = skip):
+   *   d_chunk_at    [n_queries * n_blocks_per_query] uint32: final
+   *                 AuditThreshold of each (query, object range) block;
+   *   d_stats       [8] uint64 accumulated: 0 gate passes, 1 hash-table
+   *                 inserts, 2 blocks that fell back to a Bitmap-Counter
+   *                 selection, 3 seeded queries rerun, 4 blocks launched. */
+  uint32_t* d_chunk_at;
+  unsigned long long* d_stats;
+  /* Output: number of object ranges per query used (host pointer, may be NULL). */
+  uint32_t* h_blocks_per_query;
+  /* Optional cudaEvent_t pair (as void*, NULL = none) recorded on `stream`
+   * immediately before and after the scan kernel of the first pass, so a
+   * caller can time that kernel alone with cudaEventElapsedTime. */
+  void* scan_event_begin;
+  void* scan_event_end;
+} genie_search_opts;
+
+/*
+ * Top-k of every query.
+ *   k          1 .. GENIE_MAX_K: result slots per query (row stride).
+ *   d_k        NULL, or [n_queries] uint32 device per-query k_q in 1..k.
+ *   opts       NULL for defaults.
+ *   d_ids, d_counts [n_queries * k] uint32, d_n_valid [n_queries] uint32:
+ *              device outputs, written completely.
+ * Enqueued on `stream`; without seeds the call does not synchronise.  Scratch
+ * memory is allocated stream-ordered (cudaMallocAsync) and released before
+ * return.  Searches on different streams may share one index (read-only).
+ * Errors: INVALID_ARG (k, handles from another index), OUT_OF_MEMORY, CUDA.
+ */
+genie_status genie_search(const genie_index* index, const genie_queries* queries, uint32_t k,
+                          const uint32_t* d_k, const genie_search_opts* opts, uint32_t* d_ids,
+                          uint32_t* d_counts, uint32_t* d_n_valid, genie_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GENIE_H */

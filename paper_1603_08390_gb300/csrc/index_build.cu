@@ -1,0 +1,337 @@
+// Device-side construction of the inverted index (Sec. 3.2, Fig. 3) and of
+// the sublist map (Sec. 3.2.1).
+//
+// The paper builds its index on the CPU (Table 2, "Index-build").  Here the
+// transposition object -> keywords into keyword -> objects is a stable LSD
+// radix sort of the (keyword, object id) pairs by keyword, one bit per pass
+// (count zeros per tile, scan the tile counts, scatter).  The pairs enter in
+// ascending object id, so stability leaves every postings list in ascending id
+// order, which the block-per-object-range scan depends on.
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "device_util.cuh"
+#include "internal.h"
+
+namespace genie {
+namespace {
+
+constexpr uint32_t kSplitThreads = 256;
+constexpr uint32_t kSplitItems = 16;
+constexpr uint32_t kSplitTile = kSplitThreads * kSplitItems;
+
+enum BuildFlag { kBadOffsets = 0, kBadKeyword = 1, kMaxLen = 2, kDuplicate = 3, kNumFlags = 4 };
+
+__global__ void validate_objects_kernel(const uint32_t* __restrict__ off, const uint32_t* __restrict__ kw,
+                                        uint32_t n_obj, uint64_t nnz, uint32_t vocab,
+                                        uint32_t* flags) {
+  uint32_t max_len = 0;
+  bool bad_off = false, bad_kw = false;
+  for (uint64_t o = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; o < n_obj;
+       o += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t a = off[o], b = off[o + 1];
+    if (b < a || b > nnz) {
+      bad_off = true;
+      continue;
+    }
+    max_len = max(max_len, b - a);
+    for (uint32_t e = a; e < b; ++e) bad_kw |= kw[e] >= vocab;
+  }
+  if (bad_off) atomicOr(&flags[kBadOffsets], 1u);
+  if (bad_kw) atomicOr(&flags[kBadKeyword], 1u);
+  atomicMax(&flags[kMaxLen], max_len);
+}
+
+// keys[e] = keyword, vals[e] = object id of posting e (object order).
+__global__ void expand_pairs_kernel(const uint32_t* __restrict__ off, const uint32_t* __restrict__ kw,
+                                    uint32_t n_obj, uint32_t* __restrict__ keys,
+                                    uint32_t* __restrict__ vals) {
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < n_obj; o += warps) {
+    uint32_t a = off[o], b = off[o + 1];
+    for (uint32_t e = a + dev::lane_id(); e < b; e += 32) {
+      keys[e] = kw[e];
+      vals[e] = o;
+    }
+  }
+}
+
+// zeros of bit `bit` per tile of kSplitTile keys
+__global__ void split_count_kernel(const uint32_t* __restrict__ keys, uint32_t n, int bit,
+                                   uint32_t* __restrict__ tile_zeros) {
+  __shared__ uint32_t scratch[33];
+  uint64_t start = (uint64_t)blockIdx.x * kSplitTile;
+  uint32_t z = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < kSplitItems; ++j) {
+    uint64_t i = start + j * kSplitThreads + threadIdx.x;
+    if (i < n) z += ((keys[i] >> bit) & 1u) ^ 1u;
+  }
+  uint32_t total = dev::block_sum(z, scratch);
+  if (threadIdx.x == 0) tile_zeros[blockIdx.x] = total;
+}
+
+}  // namespace
+
+// exclusive scan of n values in place, total into *total (one block)
+__global__ void scan_small_kernel(uint32_t* __restrict__ v, uint32_t n, uint32_t* total) {
+  __shared__ uint32_t scratch[33];
+  const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+  const uint32_t a = min(n, threadIdx.x * per), b = min(n, a + per);
+  uint32_t s = 0;
+  for (uint32_t i = a; i < b; ++i) s += v[i];
+  uint32_t tot;
+  uint32_t base = dev::block_exclusive_scan(s, scratch, &tot);
+  for (uint32_t i = a; i < b; ++i) {
+    uint32_t x = v[i];
+    v[i] = base;
+    base += x;
+  }
+  if (threadIdx.x == 0) *total = tot;
+}
+
+void launch_exclusive_scan(uint32_t* v, uint32_t n, uint32_t* total, cudaStream_t s) {
+  scan_small_kernel<<<1, 1024, 0, s>>>(v, n, total);
+}
+
+namespace {
+
+// stable split by bit: zeros first, then ones, each in input order
+__global__ void split_scatter_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                                     uint32_t n, int bit, const uint32_t* __restrict__ tile_zero_base,
+                                     const uint32_t* __restrict__ total_zeros,
+                                     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
+  __shared__ uint32_t scratch[33];
+  const uint64_t tile_start = (uint64_t)blockIdx.x * kSplitTile;
+  const uint64_t my = tile_start + (uint64_t)threadIdx.x * kSplitItems;
+  uint32_t k[kSplitItems], v[kSplitItems];
+  uint32_t z = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < kSplitItems; ++j) {
+    bool ok = my + j < n;
+    k[j] = ok ? keys[my + j] : 0xFFFFFFFFu;
+    v[j] = ok ? vals[my + j] : 0u;
+    if (ok) z += ((k[j] >> bit) & 1u) ^ 1u;
+  }
+  uint32_t tot;
+  uint32_t zbefore = dev::block_exclusive_scan(z, scratch, &tot);
+  const uint32_t zbase = tile_zero_base[blockIdx.x];
+  const uint32_t tz = *total_zeros;
+  // ones before this thread in the tile = items before it - zeros before it
+  uint32_t obase = tz + (uint32_t)(tile_start - zbase) + threadIdx.x * kSplitItems - zbefore;
+  uint32_t zi = zbase + zbefore;
+#pragma unroll
+  for (uint32_t j = 0; j < kSplitItems; ++j) {
+    if (my + j >= n) break;
+    uint32_t dst = ((k[j] >> bit) & 1u) ? obase++ : zi++;
+    keys_out[dst] = k[j];
+    vals_out[dst] = v[j];
+  }
+}
+
+__global__ void check_duplicates_kernel(const uint32_t* __restrict__ keys,
+                                        const uint32_t* __restrict__ vals, uint32_t n,
+                                        uint32_t* flags) {
+  bool dup = false;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x + 1; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    dup |= keys[i] == keys[i - 1] && vals[i] == vals[i - 1];
+  if (dup) atomicOr(&flags[kDuplicate], 1u);
+}
+
+// kw_off[v] = first position whose key >= v (Position Map)
+__global__ void list_offsets_kernel(const uint32_t* __restrict__ keys, uint32_t n, uint32_t vocab,
+                                    uint64_t* __restrict__ kw_off) {
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v <= vocab;
+       v += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+      uint32_t mid = lo + ((hi - lo) >> 1);
+      if (keys[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    kw_off[v] = lo;
+  }
+}
+
+// chunk_pos[v*(nch+1) + c] = first position in list v of an id >= c << shift
+__global__ void sublist_map_kernel(const uint64_t* __restrict__ kw_off, const uint32_t* __restrict__ ids,
+                                   uint32_t vocab, uint32_t nch, uint32_t shift,
+                                   uint32_t* __restrict__ chunk_pos) {
+  const uint64_t total = (uint64_t)vocab * (nch + 1);
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t v = (uint32_t)(t / (nch + 1));
+    uint32_t c = (uint32_t)(t % (nch + 1));
+    uint64_t a = kw_off[v], b = kw_off[v + 1];
+    uint64_t want = (uint64_t)c << shift;
+    uint64_t lo = a, hi = b;
+    while (lo < hi) {
+      uint64_t mid = lo + ((hi - lo) >> 1);
+      if ((uint64_t)ids[mid] < want) lo = mid + 1; else hi = mid;
+    }
+    chunk_pos[t] = (uint32_t)(lo - a);
+  }
+}
+
+int grid_for(uint64_t n, int threads, int cap = 152 * 32) {
+  uint64_t g = (n + threads - 1) / threads;
+  return (int)std::max<uint64_t>(1, std::min<uint64_t>(g, (uint64_t)cap));
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() { if (p) cudaFree(p); }
+};
+
+}  // namespace
+}  // namespace genie
+
+using namespace genie;
+
+extern "C" genie_status genie_build_index(const uint32_t* d_obj_off, const uint32_t* d_obj_kw,
+                                          uint32_t n_objects, uint32_t vocab,
+                                          uint32_t chunk_shift, genie_stream stream,
+                                          genie_index** out) {
+  if (!out) return fail(GENIE_ERR_INVALID_ARG, "genie_build_index: out is NULL");
+  if (!d_obj_off) return fail(GENIE_ERR_INVALID_ARG, "genie_build_index: d_obj_off is NULL");
+  if (n_objects == 0 || n_objects > (1u << 31))
+    return fail(GENIE_ERR_INVALID_ARG, "genie_build_index: n_objects must be in 1..2^31");
+  if (vocab == 0 || vocab > (1u << 31))
+    return fail(GENIE_ERR_INVALID_ARG, "genie_build_index: vocab must be in 1..2^31");
+  if (chunk_shift == 0) chunk_shift = 15;
+  if (chunk_shift < 12 || chunk_shift > 20)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_build_index: chunk_shift must be 0 or 12..20");
+  cudaStream_t s = as_stream(stream);
+
+  uint32_t ends[2];
+  GENIE_CUDA_TRY(cudaMemcpyAsync(&ends[0], d_obj_off, 4, cudaMemcpyDeviceToHost, s));
+  GENIE_CUDA_TRY(cudaMemcpyAsync(&ends[1], d_obj_off + n_objects, 4, cudaMemcpyDeviceToHost, s));
+  GENIE_CUDA_TRY(cudaStreamSynchronize(s));
+  if (ends[0] != 0) return fail(GENIE_ERR_INVALID_ARG, "genie_build_index: d_obj_off[0] != 0");
+  const uint32_t nnz = ends[1];
+  if (nnz > 0xFFFFFFF0u) return fail(GENIE_ERR_INVALID_ARG, "genie_build_index: too many postings");
+  if (nnz > 0 && !d_obj_kw) return fail(GENIE_ERR_INVALID_ARG, "genie_build_index: d_obj_kw is NULL");
+
+  DevBuf flags_b, keys_a, keys_b, vals_a, vals_b, tiles_b;
+  GENIE_CUDA_TRY(cudaMalloc(&flags_b.p, 64));
+  uint32_t* flags = (uint32_t*)flags_b.p;
+  GENIE_CUDA_TRY(cudaMemsetAsync(flags, 0, 64, s));
+  validate_objects_kernel<<<grid_for(n_objects, 256), 256, 0, s>>>(d_obj_off, d_obj_kw, n_objects,
+                                                                    nnz, vocab, flags);
+  GENIE_CUDA_TRY(cudaGetLastError());
+  uint32_t hflags[kNumFlags];
+  GENIE_CUDA_TRY(cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, s));
+  GENIE_CUDA_TRY(cudaStreamSynchronize(s));
+  if (hflags[kBadOffsets]) return fail(GENIE_ERR_INVALID_ARG, "genie_build_index: object offsets are not non-decreasing within [0, nnz]");
+  if (hflags[kBadKeyword]) return fail(GENIE_ERR_INVALID_ARG, "genie_build_index: a keyword id is >= vocab");
+
+  const uint64_t padded = ((uint64_t)nnz + 3) / 4 * 4 + 4;  // aligned 16-byte loads stay inside
+  GENIE_CUDA_TRY(cudaMalloc(&keys_a.p, std::max<uint64_t>(nnz, 1) * 4));
+  GENIE_CUDA_TRY(cudaMalloc(&keys_b.p, std::max<uint64_t>(nnz, 1) * 4));
+  GENIE_CUDA_TRY(cudaMalloc(&vals_a.p, padded * 4));
+  GENIE_CUDA_TRY(cudaMalloc(&vals_b.p, padded * 4));
+  const uint32_t n_tiles = (uint32_t)((nnz + kSplitTile - 1) / kSplitTile);
+  GENIE_CUDA_TRY(cudaMalloc(&tiles_b.p, (uint64_t)(n_tiles + 2) * 4));
+  uint32_t* tile_zeros = (uint32_t*)tiles_b.p;
+  uint32_t* total_zeros = tile_zeros + n_tiles + 1;
+
+  uint32_t *ka = (uint32_t*)keys_a.p, *kb = (uint32_t*)keys_b.p;
+  uint32_t *va = (uint32_t*)vals_a.p, *vb = (uint32_t*)vals_b.p;
+  if (nnz > 0) {
+    expand_pairs_kernel<<<grid_for((uint64_t)n_objects * 32, 256), 256, 0, s>>>(d_obj_off, d_obj_kw,
+                                                                               n_objects, ka, va);
+    GENIE_CUDA_TRY(cudaGetLastError());
+    int bits = 0;
+    while (bits < 32 && ((uint64_t)1 << bits) < vocab) ++bits;
+    for (int bit = 0; bit < bits; ++bit) {
+      split_count_kernel<<<n_tiles, kSplitThreads, 0, s>>>(ka, nnz, bit, tile_zeros);
+      scan_small_kernel<<<1, 1024, 0, s>>>(tile_zeros, n_tiles, total_zeros);
+      split_scatter_kernel<<<n_tiles, kSplitThreads, 0, s>>>(ka, va, nnz, bit, tile_zeros,
+                                                              total_zeros, kb, vb);
+      GENIE_CUDA_TRY(cudaGetLastError());
+      std::swap(ka, kb);
+      std::swap(va, vb);
+    }
+    check_duplicates_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(ka, va, nnz, flags);
+    GENIE_CUDA_TRY(cudaGetLastError());
+  }
+  GENIE_CUDA_TRY(cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, s));
+  GENIE_CUDA_TRY(cudaStreamSynchronize(s));
+  if (hflags[kDuplicate]) return fail(GENIE_ERR_INVALID_ARG, "genie_build_index: an object repeats a keyword (objects are sets)");
+
+  genie_index* idx = new (std::nothrow) genie_index();
+  if (!idx) return fail(GENIE_ERR_OUT_OF_MEMORY, "genie_build_index: host allocation");
+  cudaGetDevice(&idx->device);
+  idx->n_objects = n_objects;
+  idx->vocab = vocab;
+  idx->nnz = nnz;
+  idx->max_object_len = hflags[kMaxLen];
+  idx->chunk_shift = chunk_shift;
+  idx->n_chunks = (uint32_t)(((uint64_t)n_objects + (1u << chunk_shift) - 1) >> chunk_shift);
+  auto cleanup = [&](genie_status st) {
+    cudaFree(idx->kw_off);
+    cudaFree(idx->chunk_pos);
+    delete idx;
+    return st;
+  };
+  cudaError_t e = cudaMalloc(&idx->kw_off, ((uint64_t)vocab + 1) * 8);
+  if (e != cudaSuccess) return cleanup(fail_cuda(e, "cudaMalloc(kw_off)"));
+  const uint64_t tab_n = (uint64_t)vocab * (idx->n_chunks + 1);
+  e = cudaMalloc(&idx->chunk_pos, tab_n * 4);
+  if (e != cudaSuccess) return cleanup(fail_cuda(e, "cudaMalloc(chunk_pos)"));
+
+  list_offsets_kernel<<<grid_for((uint64_t)vocab + 1, 256), 256, 0, s>>>(ka, nnz, vocab, idx->kw_off);
+  // the sorted object ids become the List Array; keep the buffer, zero its padding
+  idx->post_ids = va;
+  if (va == (uint32_t*)vals_a.p) vals_a.p = nullptr; else vals_b.p = nullptr;
+  e = cudaMemsetAsync(idx->post_ids + nnz, 0, (padded - nnz) * 4, s);
+  if (e == cudaSuccess) {
+    sublist_map_kernel<<<grid_for(tab_n, 256), 256, 0, s>>>(idx->kw_off, idx->post_ids, vocab,
+                                                            idx->n_chunks, chunk_shift, idx->chunk_pos);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(idx->post_ids);
+    return cleanup(fail_cuda(e, "genie_build_index kernels"));
+  }
+  idx->device_bytes = ((uint64_t)vocab + 1) * 8 + padded * 4 + tab_n * 4;
+  *out = idx;
+  return GENIE_OK;
+}
+
+extern "C" void genie_index_destroy(genie_index* index) {
+  if (!index) return;
+  cudaDeviceSynchronize();
+  cudaFree(index->kw_off);
+  cudaFree(index->post_ids);
+  cudaFree(index->chunk_pos);
+  delete index;
+}
+
+extern "C" genie_status genie_index_get_info(const genie_index* index, genie_index_info* out) {
+  if (!index || !out) return fail(GENIE_ERR_INVALID_ARG, "genie_index_get_info: NULL argument");
+  out->n_objects = index->n_objects;
+  out->vocab = index->vocab;
+  out->nnz = index->nnz;
+  out->max_object_len = index->max_object_len;
+  out->chunk_shift = index->chunk_shift;
+  out->n_chunks = index->n_chunks;
+  out->reserved = 0;
+  out->device_bytes = index->device_bytes;
+  return GENIE_OK;
+}
+
+extern "C" genie_status genie_index_export(const genie_index* index, uint64_t* d_kw_off,
+                                           uint32_t* d_post_ids, genie_stream stream) {
+  if (!index) return fail(GENIE_ERR_INVALID_ARG, "genie_index_export: index is NULL");
+  cudaStream_t s = as_stream(stream);
+  if (d_kw_off)
+    GENIE_CUDA_TRY(cudaMemcpyAsync(d_kw_off, index->kw_off, ((uint64_t)index->vocab + 1) * 8,
+                                   cudaMemcpyDeviceToDevice, s));
+  if (d_post_ids && index->nnz)
+    GENIE_CUDA_TRY(cudaMemcpyAsync(d_post_ids, index->post_ids, index->nnz * 4,
+                                   cudaMemcpyDeviceToDevice, s));
+  return GENIE_OK;
+}

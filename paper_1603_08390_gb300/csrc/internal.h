@@ -1,0 +1,65 @@
+// Host-side definitions shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/genie.h"
+
+namespace genie {
+
+// Records `msg` as the calling thread's last error and returns `status`.
+genie_status fail(genie_status status, const std::string& msg);
+genie_status fail_cuda(cudaError_t err, const char* what);
+
+// Exclusive prefix sum of v[0..n) in place on the device, total into *total.
+void launch_exclusive_scan(uint32_t* v, uint32_t n, uint32_t* total, cudaStream_t s);
+
+inline cudaStream_t as_stream(genie_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace genie
+
+#define GENIE_CUDA_TRY(expr)                                           \
+  do {                                                                 \
+    cudaError_t genie_err_ = (expr);                                   \
+    if (genie_err_ != cudaSuccess) return genie::fail_cuda(genie_err_, #expr); \
+  } while (0)
+
+// The inverted index (Sec. 3.2): List Array, Position Map and the sublist map
+// of Sec. 3.2.1, all resident in device memory.
+struct genie_index {
+  int device = 0;
+  uint32_t n_objects = 0;
+  uint32_t vocab = 0;
+  uint64_t nnz = 0;
+  uint32_t max_object_len = 0;
+  uint32_t chunk_shift = 15;
+  uint32_t n_chunks = 0;
+  uint64_t* kw_off = nullptr;    // [vocab + 1]: list of keyword v = post_ids[kw_off[v] .. kw_off[v+1])
+  uint32_t* post_ids = nullptr;  // [nnz rounded up to 4, + 4]: ascending ids per list, zero padded
+  uint32_t* chunk_pos = nullptr; // [vocab * (n_chunks + 1)]: first position of ids >= c << chunk_shift, relative to kw_off[v]
+  uint64_t device_bytes = 0;
+};
+
+// Compiled queries: every query is a list of keywords (relational items
+// already expanded), with its count bound, scan volume and features.
+struct genie_queries {
+  const genie_index* index = nullptr;
+  int device = 0;
+  uint32_t n_queries = 0;
+  uint32_t max_bound = 0;
+  uint64_t n_keywords = 0;
+  uint64_t n_entries = 0;
+  uint32_t* q_off = nullptr;     // [n_queries + 1]
+  uint32_t* q_kw = nullptr;      // [n_keywords]
+  uint32_t* bound = nullptr;     // [n_queries]
+  uint64_t* entries = nullptr;   // [n_queries]
+  float* features = nullptr;     // [n_queries * 64]
+};
+
+namespace genie {
+constexpr uint32_t kFeatures = 64;
+constexpr float kFeatureScale = 1.0f / 32.0f;
+}  // namespace genie

@@ -1,0 +1,646 @@
+// The search hot path: postings-list scan fused with the count priority queue
+// (Sec. 3.2, Sec. 3.3, Algorithm 1, Theorem 3.1) and the exact top-k read-out.
+//
+// GB300 layout.  The paper keeps one Bitmap Counter per query in global
+// memory and lets one block scan one query item.  Here one thread block owns
+// one (query, object-id range) pair and keeps that range's Bitmap Counter,
+// ZipperArray, AuditThreshold and Hash Table in shared memory, so every
+// counter update is an on-chip sub-word atomic.  The object-id range is a
+// union of the sublists of Sec. 3.2.1 (the index stores, per keyword, where
+// each range of 2^chunk_shift ids starts), so a block reads exactly the
+// postings of its range: lists are contiguous and read with aligned 16-byte
+// loads, one warp per tile.  Blocks are ordered range-major so that the blocks
+// resident at one time share one range of the List Array in L2.
+//
+// Each range yields its own exact top-k (Theorem 3.1 per range); a second
+// kernel merges the ranges of a query, which is the per-part merge of the
+// multiple-loading method (Sec. 3.4) done on the device.
+//
+// Readings (the paper is silent or loose on these):
+//  * Gate: a posting that raises an object's count to val passes the Gate
+//    when val >= AT (Algorithm 1); AT is read without locking, and a stale
+//    (smaller) AT only lets more objects through.  ZA[val] counts passes; AT
+//    only grows (atomicMax), and a final pass sets AT_f = min{i >= AT :
+//    ZA[i] < k}.  For i >= AT_f, ZA[i] is exactly the number of objects with
+//    count >= i, so AT_f - 1 is the k-th count (Theorem 3.1).
+//  * Hash Table: keyed by object id, value = the count seen at insertion; an
+//    entry whose count is below AT - 1 may be overwritten (Sec. 3.3.2).  A
+//    pass at level val inserts only while ZA[val] < k before its own
+//    increment: once k objects reached val, an object at val can enter the
+//    top-k only through a later pass at a higher level or as a tie, and ties
+//    are read from the Bitmap Counter.  Every object with count >= AT_f
+//    keeps an entry with its exact count.
+//  * Ties at the k-th count are filled in ascending object id from the
+//    Bitmap Counter (the paper breaks them randomly).  If the Hash Table ever
+//    runs out of slots, the block selects from the Bitmap Counter alone
+//    (histogram of counts, then the same ascending-id rule).
+#include <algorithm>
+#include <cstdio>
+
+#include "device_util.cuh"
+#include "internal.h"
+
+namespace genie {
+namespace {
+
+constexpr uint32_t kKwBatch = 512;  // query keywords staged in shared memory per round
+constexpr uint32_t kUnroll = 4;     // 16-byte loads in flight per lane
+constexpr uint32_t kTile = 32 * 4 * kUnroll;  // postings per warp tile (16-byte aligned)
+
+struct ScanArgs {
+  const uint64_t* kw_off;
+  const uint32_t* post_ids;
+  const uint32_t* chunk_pos;
+  uint32_t n_chunks;
+  uint32_t chunk_shift;
+  uint32_t n_objects;
+  const uint32_t* q_off;
+  const uint32_t* q_kw;
+  const uint32_t* bound;
+  const uint32_t* q_sel;  // NULL: block query index = query id
+  uint32_t n_sel;
+  uint32_t k;             // row stride of the candidate lists
+  const uint32_t* k_arr;  // per-query k or NULL
+  const uint32_t* seed;   // per-query AuditThreshold seed or NULL
+  uint32_t block_shift;
+  uint32_t chunks_per_block;
+  uint32_t n_groups;
+  uint32_t ht_slots;
+  uint32_t za_len;
+  unsigned long long* cand;  // [n_sel][n_groups][k]
+  uint32_t* chunk_at;        // [n_sel][n_groups] or NULL
+  unsigned long long* stats;
+};
+
+size_t scan_smem_bytes(uint32_t log2w, uint32_t block_shift, uint32_t ht_slots, uint32_t za_len) {
+  size_t words = ((size_t)1 << block_shift) >> (5 - log2w);
+  return words * 4 + (size_t)ht_slots * 16 + (size_t)za_len * 4 + (3 * kKwBatch + 4) * 4;
+}
+
+__device__ __forceinline__ uint32_t vld(const uint32_t* p) { return *(const volatile uint32_t*)p; }
+
+// First `limit` lanes (ascending id) whose count equals `value` (or exceeds it
+// when GREATER) become result keys dst[0..); returns how many were written.
+template <int LOG2W, bool GREATER>
+__device__ uint32_t collect_lanes(const uint32_t* bc, uint32_t nwords, uint32_t value,
+                                  uint32_t limit, uint32_t obj_base, unsigned long long* dst,
+                                  uint32_t* scratch) {
+  constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, MASK = (1u << W) - 1u;
+  const uint32_t per = (nwords + blockDim.x - 1) / blockDim.x;
+  const uint32_t wa = min(nwords, threadIdx.x * per), wb = min(nwords, wa + per);
+  uint32_t m = 0;
+  for (uint32_t w = wa; w < wb; ++w) {
+    uint32_t word = bc[w];
+#pragma unroll
+    for (uint32_t l = 0; l < PER; ++l) {
+      uint32_t v = (word >> (l * W)) & MASK;
+      m += GREATER ? (v > value) : (v == value);
+    }
+  }
+  uint32_t total;
+  uint32_t pos = dev::block_exclusive_scan(m, scratch, &total);
+  if (pos < limit) {
+    for (uint32_t w = wa; w < wb && pos < limit; ++w) {
+      uint32_t word = bc[w];
+#pragma unroll
+      for (uint32_t l = 0; l < PER; ++l) {
+        uint32_t v = (word >> (l * W)) & MASK;
+        if ((GREATER ? (v > value) : (v == value)) && pos < limit)
+          dst[pos++] = dev::result_key(v, obj_base + w * PER + l);
+      }
+    }
+  }
+  return min(total, limit);
+}
+
+template <int LOG2W>
+__global__ void __launch_bounds__(1024, 1) scan_cpq_kernel(const ScanArgs A) {
+  constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, LPW = 5 - LOG2W, MASK = (1u << W) - 1u;
+  extern __shared__ uint4 smem_raw[];
+  __shared__ uint32_t s_at, s_overflow, s_err, s_n;
+  __shared__ uint32_t scratch[33];
+  __shared__ unsigned long long scratch64[33];
+
+  const uint32_t nwords = (1u << A.block_shift) >> LPW;
+  uint32_t* bc = reinterpret_cast<uint32_t*>(smem_raw);
+  unsigned long long* ht = reinterpret_cast<unsigned long long*>(bc + nwords);
+  unsigned long long* cand = ht + A.ht_slots;
+  uint32_t* za = reinterpret_cast<uint32_t*>(cand + A.ht_slots);
+  uint32_t* seg_lo = za + A.za_len;
+  uint32_t* seg_hi = seg_lo + kKwBatch;
+  uint32_t* tile_pre = seg_hi + kKwBatch;
+
+  const uint32_t tid = threadIdx.x, lane = dev::lane_id(), warp = dev::warp_id();
+  const uint32_t nwarps = blockDim.x >> 5;
+  const uint32_t qi = blockIdx.x % A.n_sel, g = blockIdx.x / A.n_sel;
+  const uint32_t q = A.q_sel ? A.q_sel[qi] : qi;
+  const uint32_t kq = A.k_arr ? A.k_arr[q] : A.k;
+  const uint32_t B = A.bound[q];
+  const uint32_t obj_base = g << A.block_shift;
+  const uint32_t n_local = min(1u << A.block_shift, A.n_objects - obj_base);
+  const uint32_t c0 = g * A.chunks_per_block, c1 = min(c0 + A.chunks_per_block, A.n_chunks);
+  const uint32_t ht_mask = A.ht_slots - 1, ht_bits = 31 - __clz(A.ht_slots);
+
+  // ---- reset this block's c-PQ ------------------------------------------
+  {
+    uint4* b4 = reinterpret_cast<uint4*>(bc);
+    const uint4 z4 = make_uint4(0, 0, 0, 0);
+    for (uint32_t i = tid; i < (nwords >> 2); i += blockDim.x) b4[i] = z4;
+    for (uint32_t i = tid; i < A.ht_slots; i += blockDim.x) ht[i] = 0ull;
+    for (uint32_t i = tid; i < B + 2; i += blockDim.x) za[i] = 0;
+    if (tid == 0) {
+      uint32_t s0 = A.seed ? A.seed[q] : 1u;
+      s_at = max(1u, min(s0, B + 1));
+      s_overflow = 0;
+      s_err = 0;
+    }
+  }
+  __syncthreads();
+
+  uint32_t n_gate = 0, n_ins = 0;
+
+  // Gate of Algorithm 1 for one posting that raised object `id` to `val`.
+  auto gate = [&](uint32_t id, uint32_t val) {
+    if (val > B) {  // cannot happen with a valid bound; keeps shared memory safe
+      s_err = 1;
+      return;
+    }
+    ++n_gate;
+    uint32_t z = atomicAdd(&za[val], 1u);
+    if (z < kq) {
+      ++n_ins;
+      const unsigned long long mine = ((unsigned long long)val << 32) | id;
+      uint32_t slot = ht_bits ? (id * 2654435761u) >> (32 - ht_bits) : 0u;
+      bool done = false;
+      for (uint32_t probe = 0; probe < A.ht_slots && !done; ++probe, slot = (slot + 1) & ht_mask) {
+        unsigned long long e = *(volatile unsigned long long*)&ht[slot];
+        for (;;) {
+          uint32_t ecount = (uint32_t)(e >> 32), eid = (uint32_t)e;
+          if (ecount != 0 && eid == id) {
+            if (ecount >= val) { done = true; break; }
+          } else if (!(ecount == 0 || ecount + 1 < vld(&s_at))) {
+            break;  // a live entry of another object: probe on
+          }
+          unsigned long long prev = atomicCAS(&ht[slot], e, mine);
+          if (prev == e) { done = true; break; }
+          e = prev;
+        }
+      }
+      if (!done) s_overflow = 1;
+    }
+    if (z + 1 >= kq) {  // advance AT while its level is full
+      uint32_t a = vld(&s_at);
+      while (a <= B && vld(&za[a]) >= kq) {
+        atomicMax(&s_at, a + 1);
+        ++a;
+      }
+    }
+  };
+
+  // ---- scan: all postings of the query's keywords inside this id range ---
+  const uint32_t qa = A.q_off[q], qb = A.q_off[q + 1];
+  const uint32_t stride = A.n_chunks + 1;
+  for (uint32_t kb = qa; kb < qb; kb += kKwBatch) {
+    const uint32_t nk = min(kKwBatch, qb - kb);
+    uint32_t ntiles = 0;
+    if (tid < nk) {
+      const uint32_t kw = A.q_kw[kb + tid];
+      const uint64_t base = A.kw_off[kw];
+      const uint32_t* row = A.chunk_pos + (uint64_t)kw * stride;
+      const uint32_t lo = (uint32_t)(base + row[c0]), hi = (uint32_t)(base + row[c1]);
+      seg_lo[tid] = lo;
+      seg_hi[tid] = hi;
+      ntiles = hi > lo ? (hi - (lo & ~3u) + kTile - 1) / kTile : 0;
+    }
+    uint32_t total_tiles;
+    uint32_t pre = dev::block_exclusive_scan(ntiles, scratch, &total_tiles);
+    if (tid < nk) tile_pre[tid] = pre;
+    __syncthreads();
+
+    for (uint32_t t = warp; t < total_tiles; t += nwarps) {
+      uint32_t lo_j = 0, hi_j = nk;  // last j with tile_pre[j] <= t
+      while (hi_j - lo_j > 1) {
+        uint32_t mid = (lo_j + hi_j) >> 1;
+        if (tile_pre[mid] <= t) lo_j = mid; else hi_j = mid;
+      }
+      const uint32_t lo = seg_lo[lo_j], hi = seg_hi[lo_j];
+      const uint32_t start = (lo & ~3u) + (t - tile_pre[lo_j]) * kTile;
+      uint4 v[kUnroll];
+#pragma unroll
+      for (uint32_t u = 0; u < kUnroll; ++u) {
+        const uint32_t idx = start + (u * 32 + lane) * 4;
+        v[u] = idx < hi ? __ldg(reinterpret_cast<const uint4*>(A.post_ids + idx))
+                        : make_uint4(0, 0, 0, 0);
+      }
+      uint32_t old[4 * kUnroll];
+      uint32_t valid = 0;  // bit i: element i is a posting of this tile
+#pragma unroll
+      for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
+        const uint32_t u = i >> 2, e = i & 3;
+        const uint32_t pos = start + (u * 32 + lane) * 4 + e;
+        const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
+        const uint32_t local = id - obj_base;
+        old[i] = 0;
+        if (pos >= lo && pos < hi) {
+          if (local < n_local) {
+            old[i] = atomicAdd(&bc[local >> LPW], 1u << ((local & (PER - 1)) << LOG2W));
+            valid |= 1u << i;
+          } else {
+            s_err = 1;  // an id outside this block's range: the index is inconsistent
+          }
+        }
+      }
+      uint32_t at_c = vld(&s_at);
+#pragma unroll
+      for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
+        if (!(valid & (1u << i))) continue;
+        const uint32_t u = i >> 2, e = i & 3;
+        const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
+        const uint32_t local = id - obj_base;
+        const uint32_t val = ((old[i] >> ((local & (PER - 1)) << LOG2W)) & MASK) + 1u;
+        if (val >= at_c) {
+          at_c = vld(&s_at);
+          if (val >= at_c) gate(id, val);
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- finalise AT (Lemma 3.1) and read out this range's top-k ----------
+  if (tid == 0) {
+    uint32_t a = s_at;
+    while (a <= B && za[a] >= kq) ++a;
+    s_at = a;
+    s_n = 0;
+  }
+  __syncthreads();
+  const uint32_t at_f = s_at;
+  const uint32_t nwords_local = (n_local + PER - 1) / PER;
+  unsigned long long* out = A.cand + ((unsigned long long)qi * A.n_groups + g) * A.k;
+  uint32_t n_hi, tie_v;
+  if (!s_overflow) {
+    // Theorem 3.1: the objects with count >= AT_f are in the HT (exact count
+    // re-read from the Bitmap Counter; duplicates of one id collapse below)
+    for (uint32_t i = tid; i < A.ht_slots; i += blockDim.x) {
+      unsigned long long e = ht[i];
+      uint32_t c = (uint32_t)(e >> 32);
+      if (c != 0 && c >= at_f) {
+        uint32_t id = (uint32_t)e, local = id - obj_base;
+        uint32_t exact = (bc[local >> LPW] >> ((local & (PER - 1)) << LOG2W)) & MASK;
+        cand[atomicAdd(&s_n, 1u)] = dev::result_key(exact, id);
+      }
+    }
+    __syncthreads();
+    const uint32_t n = s_n, n2 = dev::next_pow2(max(n, 1u));
+    for (uint32_t i = n + tid; i < n2; i += blockDim.x) cand[i] = 0ull;
+    __syncthreads();
+    dev::bitonic_sort_desc(cand, n2);
+    if (tid == 0) {
+      uint32_t w = 0;
+      for (uint32_t i = 0; i < n; ++i)
+        if (w == 0 || cand[i] != cand[w - 1]) cand[w++] = cand[i];
+      s_n = min(w, kq);
+    }
+    __syncthreads();
+    n_hi = s_n;
+    tie_v = at_f - 1;  // 0 when AT_f = 1: no ties to add
+  } else {
+    // Bitmap-Counter selection: histogram of counts in ZA's storage
+    for (uint32_t i = tid; i < B + 2; i += blockDim.x) za[i] = 0;
+    __syncthreads();
+    for (uint32_t w = tid; w < nwords_local; w += blockDim.x) {
+      uint32_t word = bc[w];
+#pragma unroll
+      for (uint32_t l = 0; l < PER; ++l) {
+        uint32_t v = (word >> (l * W)) & MASK;
+        if (v) atomicAdd(&za[min(v, B + 1)], 1u);
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t cum = 0, t = 1;
+      for (uint32_t v = B + 1; v >= 1; --v) {
+        if (cum + za[v] >= kq) { t = v; break; }
+        cum += za[v];
+      }
+      s_n = t;
+    }
+    __syncthreads();
+    tie_v = s_n;
+    n_hi = collect_lanes<LOG2W, true>(bc, nwords_local, tie_v, kq, obj_base, cand, scratch);
+    __syncthreads();
+    const uint32_t n2 = dev::next_pow2(max(n_hi, 1u));
+    for (uint32_t i = n_hi + tid; i < n2; i += blockDim.x) cand[i] = 0ull;
+    __syncthreads();
+    dev::bitonic_sort_desc(cand, n2);
+  }
+  for (uint32_t i = tid; i < n_hi; i += blockDim.x) out[i] = cand[i];
+  uint32_t n_tie = 0;
+  if (tie_v >= 1 && n_hi < kq)
+    n_tie = collect_lanes<LOG2W, false>(bc, nwords_local, tie_v, kq - n_hi, obj_base, out + n_hi, scratch);
+  for (uint32_t i = n_hi + n_tie + tid; i < kq; i += blockDim.x) out[i] = 0ull;
+
+  if (A.chunk_at && tid == 0) A.chunk_at[(unsigned long long)qi * A.n_groups + g] = at_f;
+  if (A.stats) {
+    unsigned long long gsum = dev::block_sum((unsigned long long)n_gate, scratch64);
+    unsigned long long isum = dev::block_sum((unsigned long long)n_ins, scratch64);
+    if (tid == 0) {
+      atomicAdd(&A.stats[0], gsum);
+      atomicAdd(&A.stats[1], isum);
+      if (s_overflow) atomicAdd(&A.stats[2], 1ull);
+      atomicAdd(&A.stats[4], 1ull);
+      if (s_err) atomicAdd(&A.stats[5], 1ull);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Merge of the per-range top-k lists of each query (Sec. 3.4 merge, on device)
+// ---------------------------------------------------------------------------
+
+struct MergeArgs {
+  const unsigned long long* cand;
+  uint32_t n_sel;
+  const uint32_t* q_sel;
+  uint32_t n_groups;
+  uint32_t k;
+  const uint32_t* k_arr;
+  const uint32_t* bound;
+  uint32_t za_len;
+  uint32_t* ids;
+  uint32_t* counts;
+  uint32_t* n_valid;
+};
+
+constexpr uint32_t kMergeThreads = 256;
+
+__global__ void __launch_bounds__(kMergeThreads) merge_kernel(const MergeArgs M) {
+  extern __shared__ uint4 smem_raw[];
+  unsigned long long* buf = reinterpret_cast<unsigned long long*>(smem_raw);  // [next_pow2(k)]
+  uint32_t* hist = reinterpret_cast<uint32_t*>(buf + dev::next_pow2(M.k));    // [za_len]
+  __shared__ uint32_t s_t, s_ngt, s_r, s_n;
+  __shared__ uint32_t scratch[33];
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t qi = blockIdx.x; qi < M.n_sel; qi += gridDim.x) {
+    const uint32_t q = M.q_sel ? M.q_sel[qi] : qi;
+    const uint32_t kq = M.k_arr ? M.k_arr[q] : M.k;
+    const uint32_t B = M.bound[q];
+    const unsigned long long* lists = M.cand + (unsigned long long)qi * M.n_groups * M.k;
+    for (uint32_t i = tid; i < B + 2; i += blockDim.x) hist[i] = 0;
+    if (tid == 0) s_n = 0;
+    __syncthreads();
+    const uint32_t total_c = M.n_groups * kq;
+    for (uint32_t i = tid; i < total_c; i += blockDim.x) {
+      unsigned long long key = lists[(i / kq) * M.k + (i % kq)];
+      if (key) atomicAdd(&hist[min(dev::key_count(key), B + 1)], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t cum = 0, t = 1;
+      for (uint32_t v = B + 1; v >= 1; --v) {
+        if (cum + hist[v] >= kq) { t = v; break; }
+        cum += hist[v];
+      }
+      uint32_t ngt = 0;
+      for (uint32_t v = t + 1; v <= B + 1; ++v) ngt += hist[v];
+      s_t = t;
+      s_ngt = ngt;
+      s_r = min(kq - ngt, hist[t]);
+    }
+    __syncthreads();
+    const uint32_t t = s_t, ngt = s_ngt, r = s_r;
+    // every candidate above the k-th count
+    for (uint32_t i = tid; i < total_c; i += blockDim.x) {
+      unsigned long long key = lists[(i / kq) * M.k + (i % kq)];
+      if (key && dev::key_count(key) > t) buf[atomicAdd(&s_n, 1u)] = key;
+    }
+    __syncthreads();
+    const uint32_t n2 = dev::next_pow2(max(ngt, 1u));
+    for (uint32_t i = ngt + tid; i < n2; i += blockDim.x) buf[i] = 0ull;
+    __syncthreads();
+    dev::bitonic_sort_desc(buf, n2);
+    uint32_t* ids = M.ids + (unsigned long long)q * M.k;
+    uint32_t* cnt = M.counts + (unsigned long long)q * M.k;
+    for (uint32_t i = tid; i < ngt; i += blockDim.x) {
+      ids[i] = dev::key_id(buf[i]);
+      cnt[i] = dev::key_count(buf[i]);
+    }
+    // ties at the k-th count: range order = id order, each run ascending
+    const uint32_t per = (M.n_groups + blockDim.x - 1) / blockDim.x;
+    const uint32_t ga = min(M.n_groups, tid * per), gb = min(M.n_groups, ga + per);
+    uint32_t m = 0;
+    for (uint32_t gg = ga; gg < gb; ++gg)
+      for (uint32_t j = 0; j < kq; ++j) {
+        unsigned long long key = lists[(unsigned long long)gg * M.k + j];
+        m += key && dev::key_count(key) == t;
+      }
+    uint32_t tot;
+    uint32_t pos = dev::block_exclusive_scan(m, scratch, &tot);
+    for (uint32_t gg = ga; gg < gb && pos < r; ++gg)
+      for (uint32_t j = 0; j < kq && pos < r; ++j) {
+        unsigned long long key = lists[(unsigned long long)gg * M.k + j];
+        if (key && dev::key_count(key) == t) {
+          ids[ngt + pos] = dev::key_id(key);
+          cnt[ngt + pos] = t;
+          ++pos;
+        }
+      }
+    for (uint32_t i = ngt + r + tid; i < M.k; i += blockDim.x) {
+      ids[i] = 0xFFFFFFFFu;
+      cnt[i] = 0;
+    }
+    if (tid == 0) M.n_valid[q] = ngt + r;
+    __syncthreads();
+  }
+}
+
+// seeded search: queries whose result cannot be certified
+__global__ void verify_seeded_kernel(uint32_t n_queries, uint32_t k, const uint32_t* __restrict__ k_arr,
+                                     const uint32_t* __restrict__ seed, const uint32_t* __restrict__ counts,
+                                     const uint32_t* __restrict__ n_valid, uint32_t* __restrict__ rerun,
+                                     uint32_t* n_rerun) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n_queries; q += gridDim.x * blockDim.x) {
+    const uint32_t kq = k_arr ? k_arr[q] : k;
+    const uint32_t s = seed[q];
+    bool ok = s <= 1 || (n_valid[q] == kq && counts[(unsigned long long)q * k + kq - 1] >= s);
+    if (!ok) rerun[atomicAdd(n_rerun, 1u)] = q;
+  }
+}
+
+__global__ void add_stat_kernel(unsigned long long* stat, uint32_t v) { *stat += v; }
+
+__global__ void check_k_kernel(uint32_t n_queries, uint32_t k, const uint32_t* __restrict__ k_arr,
+                               uint32_t* bad) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n_queries; q += gridDim.x * blockDim.x)
+    if (k_arr[q] == 0 || k_arr[q] > k) atomicOr(bad, 1u);
+}
+
+struct Plan {
+  uint32_t log2w;
+  uint32_t block_shift;
+  uint32_t n_groups;
+  uint32_t ht_slots;
+  uint32_t threads;
+  uint32_t za_len;
+  size_t smem;
+};
+
+genie_status make_plan(const genie_index* idx, const genie_queries* qs, uint32_t k,
+                       const genie_search_opts* o, Plan* p) {
+  const uint32_t B = qs->max_bound;
+  p->log2w = B <= 15 ? 2u : (B <= 255 ? 3u : 4u);
+  uint32_t need = 0;
+  while (need < 31 && ((uint64_t)1 << need) < idx->n_objects) ++need;
+  uint32_t shift = 20 - p->log2w;  // 128 KB of Bitmap Counter
+  if (o && o->block_shift) shift = o->block_shift;
+  shift = std::min(shift, std::max(need, idx->chunk_shift));
+  shift = std::max(shift, idx->chunk_shift);
+  p->block_shift = shift;
+  p->n_groups = (uint32_t)(((uint64_t)idx->n_objects + (1ull << shift) - 1) >> shift);
+  uint32_t slots = (o && o->ht_slots) ? o->ht_slots : std::max(64u, dev::next_pow2(4 * k));
+  if (slots & (slots - 1)) return fail(GENIE_ERR_INVALID_ARG, "genie_search: ht_slots must be a power of two");
+  if (slots < k) return fail(GENIE_ERR_INVALID_ARG, "genie_search: ht_slots must be >= k");
+  p->ht_slots = slots;
+  p->threads = (o && o->threads) ? o->threads : 1024u;
+  if (p->threads % 32 || p->threads < kKwBatch || p->threads > 1024)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search: threads must be a multiple of 32 in 512..1024");
+  p->za_len = B + 2;
+  p->smem = scan_smem_bytes(p->log2w, shift, slots, p->za_len);
+  int dev = 0, max_smem = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (p->smem + 1024 > (size_t)max_smem)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search: block_shift / ht_slots need more shared memory than a block has");
+  return GENIE_OK;
+}
+
+template <int LOG2W>
+cudaError_t launch_scan(const ScanArgs& a, const Plan& p, cudaStream_t s) {
+  auto kern = scan_cpq_kernel<LOG2W>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  if (e != cudaSuccess) return e;
+  const uint64_t blocks = (uint64_t)a.n_sel * a.n_groups;
+  kern<<<(uint32_t)blocks, p.threads, p.smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t run_pass(const genie_index* idx, const genie_queries* qs, uint32_t k, const uint32_t* d_k,
+                     const uint32_t* seed, const uint32_t* sel, uint32_t n_sel, const Plan& p,
+                     const genie_search_opts* o, unsigned long long* cand, uint32_t* ids,
+                     uint32_t* counts, uint32_t* n_valid, cudaStream_t s) {
+  ScanArgs a;
+  a.kw_off = idx->kw_off;
+  a.post_ids = idx->post_ids;
+  a.chunk_pos = idx->chunk_pos;
+  a.n_chunks = idx->n_chunks;
+  a.chunk_shift = idx->chunk_shift;
+  a.n_objects = idx->n_objects;
+  a.q_off = qs->q_off;
+  a.q_kw = qs->q_kw;
+  a.bound = qs->bound;
+  a.q_sel = sel;
+  a.n_sel = n_sel;
+  a.k = k;
+  a.k_arr = d_k;
+  a.seed = seed;
+  a.block_shift = p.block_shift;
+  a.chunks_per_block = 1u << (p.block_shift - idx->chunk_shift);
+  a.n_groups = p.n_groups;
+  a.ht_slots = p.ht_slots;
+  a.za_len = p.za_len;
+  a.cand = cand;
+  a.chunk_at = (o && !sel) ? o->d_chunk_at : nullptr;
+  a.stats = o ? o->d_stats : nullptr;
+  const bool timed = o && !sel && o->scan_event_begin && o->scan_event_end;
+  if (timed) cudaEventRecord((cudaEvent_t)o->scan_event_begin, s);
+  cudaError_t e = p.log2w == 2 ? launch_scan<2>(a, p, s)
+                : p.log2w == 3 ? launch_scan<3>(a, p, s)
+                               : launch_scan<4>(a, p, s);
+  if (e != cudaSuccess) return e;
+  if (timed) cudaEventRecord((cudaEvent_t)o->scan_event_end, s);
+  MergeArgs m;
+  m.cand = cand;
+  m.n_sel = n_sel;
+  m.q_sel = sel;
+  m.n_groups = p.n_groups;
+  m.k = k;
+  m.k_arr = d_k;
+  m.bound = qs->bound;
+  m.za_len = p.za_len;
+  m.ids = ids;
+  m.counts = counts;
+  m.n_valid = n_valid;
+  const size_t msmem = dev::next_pow2(k) * 8 + (size_t)p.za_len * 4;
+  e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
+  if (e != cudaSuccess) return e;
+  merge_kernel<<<std::min<uint32_t>(n_sel, 152u * 16u), kMergeThreads, msmem, s>>>(m);
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace genie
+
+using namespace genie;
+
+extern "C" genie_status genie_search(const genie_index* index, const genie_queries* queries,
+                                     uint32_t k, const uint32_t* d_k, const genie_search_opts* opts,
+                                     uint32_t* d_ids, uint32_t* d_counts, uint32_t* d_n_valid,
+                                     genie_stream stream) {
+  if (!index || !queries || !d_ids || !d_counts || !d_n_valid)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search: NULL argument");
+  if (queries->index != index)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search: queries were compiled for another index");
+  if (k == 0 || k > GENIE_MAX_K) return fail(GENIE_ERR_INVALID_ARG, "genie_search: k must be in 1..GENIE_MAX_K");
+  cudaStream_t s = as_stream(stream);
+  Plan p;
+  genie_status st = make_plan(index, queries, k, opts, &p);
+  if (st != GENIE_OK) return st;
+  if (opts && opts->h_blocks_per_query) *opts->h_blocks_per_query = p.n_groups;
+  const uint32_t Q = queries->n_queries;
+  const uint64_t cand_bytes = (uint64_t)Q * p.n_groups * k * 8;
+  unsigned long long* cand = nullptr;
+  uint32_t* aux = nullptr;  // [0] flags, [1] rerun count, [2..] rerun list
+  GENIE_CUDA_TRY(cudaMallocAsync((void**)&cand, cand_bytes, s));
+  cudaError_t e = cudaMallocAsync((void**)&aux, (uint64_t)(Q + 2) * 4, s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(cand, s);
+    return fail_cuda(e, "cudaMallocAsync");
+  }
+  auto release = [&]() {
+    cudaFreeAsync(cand, s);
+    cudaFreeAsync(aux, s);
+  };
+  if (d_k) {
+    uint32_t bad = 0;
+    e = cudaMemsetAsync(aux, 0, 4, s);
+    if (e == cudaSuccess) {
+      check_k_kernel<<<std::min<uint32_t>((Q + 255) / 256, 1024u), 256, 0, s>>>(Q, k, d_k, aux);
+      e = cudaMemcpyAsync(&bad, aux, 4, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { release(); return fail_cuda(e, "genie_search: per-query k check"); }
+    if (bad) { release(); return fail(GENIE_ERR_INVALID_ARG, "genie_search: a per-query k is 0 or larger than k"); }
+  }
+  const uint32_t* seed = opts ? opts->d_seed : nullptr;
+  e = run_pass(index, queries, k, d_k, seed, nullptr, Q, p, opts, cand, d_ids, d_counts, d_n_valid, s);
+  if (e == cudaSuccess && seed) {
+    // verify-and-rerun: certified iff s = 1 or the k-th merged count >= s
+    uint32_t n_rerun = 0;
+    e = cudaMemsetAsync(aux + 1, 0, 4, s);
+    if (e == cudaSuccess) {
+      verify_seeded_kernel<<<std::min<uint32_t>((Q + 255) / 256, 1024u), 256, 0, s>>>(
+          Q, k, d_k, seed, d_counts, d_n_valid, aux + 2, aux + 1);
+      e = cudaMemcpyAsync(&n_rerun, aux + 1, 4, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && n_rerun > 0) {
+      if (opts && opts->d_stats) add_stat_kernel<<<1, 1, 0, s>>>(opts->d_stats + 3, n_rerun);
+      e = run_pass(index, queries, k, d_k, nullptr, aux + 2, n_rerun, p, opts, cand, d_ids,
+                   d_counts, d_n_valid, s);
+    }
+  }
+  release();
+  if (e != cudaSuccess) return fail_cuda(e, "genie_search");
+  return GENIE_OK;
+}

@@ -1,0 +1,247 @@
+"""Python binding of the C ABI in ``include/genie.h`` (ctypes, same names).
+
+Argument marshalling only: device buffers are passed as torch CUDA tensors
+(or raw integer addresses), streams as ``torch.cuda.Stream`` (or a raw
+``cudaStream_t`` integer; default: torch's current stream).  Every step of
+the search runs in ``libgenie.so``; if that library is missing this module
+raises instead of computing anything itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgenie.so")
+
+GENIE_OK = 0
+GENIE_ERR_INVALID_ARG = 1
+GENIE_ERR_OUT_OF_MEMORY = 2
+GENIE_ERR_CUDA = 3
+GENIE_ERR_CAPACITY = 4
+GENIE_ERR_TIMEOUT = 5
+GENIE_MAX_K = 1024
+GENIE_MAX_BOUND = 4095
+N_FEATURES = 64
+
+EXPORTED = (
+    "genie_last_error", "genie_version", "genie_build_index", "genie_index_destroy",
+    "genie_index_get_info", "genie_index_export", "genie_make_queries", "genie_compile_ranges",
+    "genie_queries_destroy", "genie_queries_get_info", "genie_queries_export", "genie_search",
+)
+
+
+class GenieError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("genie status %d: %s" % (status, message))
+        self.status = status
+
+
+class IndexInfo(ctypes.Structure):
+    _fields_ = [("n_objects", ctypes.c_uint32), ("vocab", ctypes.c_uint32),
+                ("nnz", ctypes.c_uint64), ("max_object_len", ctypes.c_uint32),
+                ("chunk_shift", ctypes.c_uint32), ("n_chunks", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64)]
+
+
+class QueriesInfo(ctypes.Structure):
+    _fields_ = [("n_queries", ctypes.c_uint32), ("max_bound", ctypes.c_uint32),
+                ("n_keywords", ctypes.c_uint64), ("n_entries", ctypes.c_uint64)]
+
+
+class SearchOpts(ctypes.Structure):
+    _fields_ = [("d_seed", ctypes.c_void_p), ("block_shift", ctypes.c_uint32),
+                ("threads", ctypes.c_uint32), ("ht_slots", ctypes.c_uint32),
+                ("d_chunk_at", ctypes.c_void_p), ("d_stats", ctypes.c_void_p),
+                ("h_blocks_per_query", ctypes.POINTER(ctypes.c_uint32)),
+                ("scan_event_begin", ctypes.c_void_p), ("scan_event_end", ctypes.c_void_p)]
+
+
+_LIB = None
+_LOCK = threading.Lock()
+
+
+def load(path: Optional[str] = None):
+    """Load libgenie.so (built by ``__graft_entry__.build()``)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise GenieError(GENIE_ERR_CUDA, "libgenie.so is not built (%s); run "
+                             "paper_1603_08390_gb300._build.build()" % p)
+        lib = ctypes.CDLL(p)
+        vp, u32, u64, st = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+        lib.genie_last_error.restype = ctypes.c_char_p
+        lib.genie_last_error.argtypes = []
+        lib.genie_version.restype = st
+        lib.genie_build_index.argtypes = [vp, vp, u32, u32, u32, vp, ctypes.POINTER(vp)]
+        lib.genie_build_index.restype = st
+        lib.genie_index_destroy.argtypes = [vp]
+        lib.genie_index_destroy.restype = None
+        lib.genie_index_get_info.argtypes = [vp, ctypes.POINTER(IndexInfo)]
+        lib.genie_index_get_info.restype = st
+        lib.genie_index_export.argtypes = [vp, vp, vp, vp]
+        lib.genie_index_export.restype = st
+        lib.genie_make_queries.argtypes = [vp, vp, vp, u32, vp, ctypes.POINTER(vp)]
+        lib.genie_make_queries.restype = st
+        lib.genie_compile_ranges.argtypes = [vp, u32, vp, vp, vp, vp, u32, vp, ctypes.POINTER(vp)]
+        lib.genie_compile_ranges.restype = st
+        lib.genie_queries_destroy.argtypes = [vp]
+        lib.genie_queries_destroy.restype = None
+        lib.genie_queries_get_info.argtypes = [vp, ctypes.POINTER(QueriesInfo)]
+        lib.genie_queries_get_info.restype = st
+        lib.genie_queries_export.argtypes = [vp, vp, vp, vp, vp]
+        lib.genie_queries_export.restype = st
+        lib.genie_search.argtypes = [vp, vp, u32, vp, ctypes.POINTER(SearchOpts), vp, vp, vp, vp]
+        lib.genie_search.restype = st
+        _LIB = lib
+        return lib
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s) -> Optional[int]:
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(status: int, lib) -> None:
+    if status != GENIE_OK:
+        raise GenieError(status, lib.genie_last_error().decode())
+
+
+def genie_last_error() -> str:
+    return load().genie_last_error().decode()
+
+
+def genie_version() -> int:
+    return load().genie_version()
+
+
+class Index:
+    """Owning wrapper of a ``genie_index*``."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+        info = IndexInfo()
+        _check(load().genie_index_get_info(handle, ctypes.byref(info)), load())
+        self.info = info
+
+    def __getattr__(self, name):
+        return getattr(self.__dict__["info"], name)
+
+    def close(self):
+        if self.handle:
+            load().genie_index_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Queries:
+    """Owning wrapper of a ``genie_queries*``."""
+
+    def __init__(self, handle: int, index: Index):
+        self.handle = handle
+        self.index = index  # keeps the index alive
+        info = QueriesInfo()
+        _check(load().genie_queries_get_info(handle, ctypes.byref(info)), load())
+        self.info = info
+
+    def __getattr__(self, name):
+        return getattr(self.__dict__["info"], name)
+
+    def close(self):
+        if self.handle:
+            load().genie_queries_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def genie_build_index(d_obj_off, d_obj_kw, n_objects: int, vocab: int, chunk_shift: int = 0,
+                      stream=None) -> Index:
+    lib = load()
+    out = ctypes.c_void_p()
+    _check(lib.genie_build_index(_ptr(d_obj_off), _ptr(d_obj_kw), n_objects, vocab, chunk_shift,
+                                 _stream(stream), ctypes.byref(out)), lib)
+    return Index(out.value)
+
+
+def genie_index_export(index: Index, d_kw_off=None, d_post_ids=None, stream=None) -> None:
+    lib = load()
+    _check(lib.genie_index_export(index.handle, _ptr(d_kw_off), _ptr(d_post_ids), _stream(stream)),
+           lib)
+
+
+def genie_make_queries(index: Index, d_q_off, d_q_kw, n_queries: int, stream=None) -> Queries:
+    lib = load()
+    out = ctypes.c_void_p()
+    _check(lib.genie_make_queries(index.handle, _ptr(d_q_off), _ptr(d_q_kw), n_queries,
+                                  _stream(stream), ctypes.byref(out)), lib)
+    return Queries(out.value, index)
+
+
+def genie_compile_ranges(index: Index, values_per_dim: int, d_item_off, d_dim, d_lo, d_hi,
+                         n_queries: int, stream=None) -> Queries:
+    lib = load()
+    out = ctypes.c_void_p()
+    _check(lib.genie_compile_ranges(index.handle, values_per_dim, _ptr(d_item_off), _ptr(d_dim),
+                                    _ptr(d_lo), _ptr(d_hi), n_queries, _stream(stream),
+                                    ctypes.byref(out)), lib)
+    return Queries(out.value, index)
+
+
+def genie_queries_export(queries: Queries, d_bound=None, d_entries=None, d_features=None,
+                         stream=None) -> None:
+    lib = load()
+    _check(lib.genie_queries_export(queries.handle, _ptr(d_bound), _ptr(d_entries),
+                                    _ptr(d_features), _stream(stream)), lib)
+
+
+def make_opts(d_seed=None, block_shift: int = 0, threads: int = 0, ht_slots: int = 0,
+              d_chunk_at=None, d_stats=None, scan_events=None) -> SearchOpts:
+    o = SearchOpts()
+    o.d_seed = _ptr(d_seed)
+    o.block_shift = block_shift
+    o.threads = threads
+    o.ht_slots = ht_slots
+    o.d_chunk_at = _ptr(d_chunk_at)
+    o.d_stats = _ptr(d_stats)
+    o._blocks = ctypes.c_uint32(0)
+    o.h_blocks_per_query = ctypes.pointer(o._blocks)
+    if scan_events is not None:  # (begin, end): torch.cuda.Event or raw cudaEvent_t
+        b, e = scan_events
+        o.scan_event_begin = b if isinstance(b, int) else b.cuda_event
+        o.scan_event_end = e if isinstance(e, int) else e.cuda_event
+    return o
+
+
+def genie_search(index: Index, queries: Queries, k: int, d_ids, d_counts, d_n_valid, d_k=None,
+                 opts: Optional[SearchOpts] = None, stream=None) -> None:
+    lib = load()
+    _check(lib.genie_search(index.handle, queries.handle, k, _ptr(d_k),
+                            ctypes.byref(opts) if opts is not None else None, _ptr(d_ids),
+                            _ptr(d_counts), _ptr(d_n_valid), _stream(stream)), lib)

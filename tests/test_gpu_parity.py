@@ -1,0 +1,323 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integer results must match bit for bit: ids, counts, padding and n_valid of
+every result slot, under the order (count desc, id asc).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle import mlp as mlp_ref
+from paper_1603_08390_gb300 import _build, genie, runner
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    _build.build()
+    genie.load()
+
+
+def assert_same(res, ref, rows=None):
+    """res: runner output dict; ref: oracle dict; rows: query ids of ref in res."""
+    karr = ref["k"]
+    n_q = len(ref["n_valid"])
+    rows = np.arange(n_q) if rows is None else np.asarray(rows)
+    stride = res["ids"].shape[1]
+    for j in range(n_q):
+        q = rows[j]
+        kq = int(karr[j])
+        n = int(ref["n_valid"][j])
+        assert res["n_valid"][q] == n, (q, res["n_valid"][q], n)
+        assert np.array_equal(res["ids"][q, :n], ref["ids"][j, :n]), q
+        assert np.array_equal(res["counts"][q, :n], ref["counts"][j, :n]), q
+        assert np.all(res["ids"][q, n:stride] == 0xFFFFFFFF), q
+        assert np.all(res["counts"][q, n:stride] == 0), q
+        assert n <= kq
+
+
+def run(w, k=None, chunk_shift=0, opts=None, index=None):
+    idx = index or runner.build_index(w, chunk_shift)
+    qs = runner.compile_queries(idx, w)
+    out = runner.search(idx, qs, w.k if k is None else k, opts=opts)
+    torch.cuda.synchronize()
+    return out.host(), idx, qs
+
+
+# ---------------------------------------------------------------------------
+# the five workload shapes at test sizes
+# ---------------------------------------------------------------------------
+
+def test_relational_tiny_config_full():
+    w = synth.config(1)
+    res, _, qs = run(w)
+    assert qs.max_bound <= 255
+    assert_same(res, oracle.topk(w))
+
+
+@pytest.mark.parametrize("block_shift", [12, 13, 0])
+def test_relational_many_ranges_ragged(block_shift):
+    w = synth.relational(n_objects=70_001, n_queries=48, config=11)
+    res, _, _ = run(w, chunk_shift=12, opts=genie.make_opts(block_shift=block_shift))
+    assert_same(res, oracle.topk(w))
+
+
+@pytest.mark.parametrize("block_shift", [12, 14, 0])
+def test_lsh_keywords_small(block_shift):
+    w = synth.lsh(60_000, 40, 100, config=12)
+    opts = genie.make_opts(block_shift=block_shift)
+    res, _, qs = run(w, chunk_shift=12, opts=opts)
+    assert qs.max_bound == 256  # 16-bit lanes
+    assert_same(res, oracle.topk(w))
+
+
+def test_zipf_sets_16bit():
+    w = synth.sets(200_000, (16, 256), 1 << 16, 96, (8, 512), 10, config=13)
+    res, _, qs = run(w)
+    assert 16 <= qs.max_bound <= 256
+    assert_same(res, oracle.topk(w))
+
+
+def test_zipf_sets_8bit_per_query_k():
+    w = synth.sets(150_000, (64, 64), 1 << 18, 64, (8, 512), 10, config=15)
+    rng = np.random.default_rng(3)
+    w.k = np.array([1, 10, 100], dtype=np.uint32)[rng.integers(0, 3, w.n_queries)]
+    res, _, qs = run(w, chunk_shift=14, opts=genie.make_opts(block_shift=15))
+    assert qs.max_bound <= 64
+    assert_same(res, oracle.topk(w))
+
+
+def test_4bit_lanes_short_queries():
+    w = synth.sets(90_000, (8, 40), 4096, 70, (1, 15), 25, config=16)
+    res, _, qs = run(w, chunk_shift=13)
+    assert qs.max_bound <= 15
+    assert_same(res, oracle.topk(w))
+
+
+# ---------------------------------------------------------------------------
+# c-PQ invariants on the device state
+# ---------------------------------------------------------------------------
+
+def test_final_audit_threshold_is_kth_count_plus_one_per_range():
+    """Theorem 3.1 per object range: AT_f - 1 is the range's k-th count."""
+    w = synth.lsh(50_000, 12, 20, config=17)
+    shift = 13
+    idx = runner.build_index(w, 12)
+    qs = runner.compile_queries(idx, w)
+    groups = (w.n_objects + (1 << shift) - 1) >> shift
+    at = torch.zeros(w.n_queries * groups, dtype=torch.int32, device="cuda")
+    opts = genie.make_opts(block_shift=shift, d_chunk_at=at)
+    runner.search(idx, qs, w.k, opts=opts)
+    at = runner.u32(at).reshape(w.n_queries, groups)
+    for g in range(groups):
+        lo, hi = g << shift, min(w.n_objects, (g + 1) << shift)
+        ref = oracle.topk(w, obj_range=(lo, hi))
+        assert np.array_equal(at[:, g] - 1, ref["tk"]), g
+
+
+def test_compiler_facts_match_the_oracle():
+    w = synth.sets(120_000, (16, 200), 1 << 15, 80, (8, 300), 10, config=18)
+    idx = runner.build_index(w)
+    qs = runner.compile_queries(idx, w)
+    facts = runner.query_facts(qs)
+    ref = oracle.topk(w)
+    # postings scanned by a query = sum over objects of its match count
+    assert np.array_equal(facts["entries"], ref["mcsum"])
+    assert qs.n_entries == int(ref["mcsum"].sum())
+    max_len = int(np.diff(w.obj_off.astype(np.int64)).max())
+    qlen = np.diff(w.q_off.astype(np.int64))
+    assert np.array_equal(facts["bound"], np.minimum(qlen, max_len))
+    assert np.all(ref["counts"].max(axis=1) <= facts["bound"])
+    df = np.bincount(w.obj_kw, minlength=w.vocab)
+    want = mlp_ref.features(df[w.q_kw], w.q_off)
+    assert np.array_equal(facts["features"], want.astype(np.float32))
+
+
+def test_index_is_the_transpose_of_the_objects():
+    w = synth.sets(30_000, (5, 60), 5000, 1, (1, 2), 1, config=19)
+    idx = runner.build_index(w)
+    kw_off = torch.empty(w.vocab + 1, dtype=torch.int64, device="cuda")
+    post = torch.empty(w.nnz, dtype=torch.int32, device="cuda")
+    genie.genie_index_export(idx, kw_off, post)
+    owner = np.repeat(np.arange(w.n_objects, dtype=np.uint32), np.diff(w.obj_off.astype(np.int64)))
+    order = np.lexsort((owner, w.obj_kw))
+    want_off = np.concatenate([[0], np.cumsum(np.bincount(w.obj_kw, minlength=w.vocab))])
+    assert np.array_equal(kw_off.cpu().numpy(), want_off)
+    assert np.array_equal(runner.u32(post), owner[order])
+    assert idx.max_object_len == int(np.diff(w.obj_off.astype(np.int64)).max())
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def _kw_workload(objects, queries, vocab, k):
+    obj_off = np.concatenate([[0], np.cumsum([len(o) for o in objects])]).astype(np.uint32)
+    q_off = np.concatenate([[0], np.cumsum([len(q) for q in queries])]).astype(np.uint32)
+    flat = lambda ll: np.array([e for x in ll for e in x], dtype=np.uint32)
+    return synth.Workload("edge", "keywords", len(objects), vocab, obj_off, flat(objects),
+                          len(queries), k, q_off=q_off, q_kw=flat(queries))
+
+
+def test_edge_cases_small():
+    objects = [[0, 1, 2], [], [1, 2], [2], [0, 2, 5], [5], [], [3, 4]]
+    queries = [[], [6], [2, 2, 2], [0, 1, 2, 5], [3], [1, 1], [7, 6], [0, 1, 2, 3, 4, 5, 6, 7]]
+    for k in (1, 2, 3, 8, 9, 50):
+        w = _kw_workload(objects, queries, 8, k)
+        res, _, _ = run(w)
+        assert_same(res, oracle.topk(w))
+
+
+def test_all_objects_tie():
+    n = 40_000
+    objects = [[7, 9] for _ in range(n)]
+    w = _kw_workload(objects, [[7], [9, 7], [1], [7, 7, 7]], 10, 100)
+    res, _, _ = run(w, chunk_shift=12, opts=genie.make_opts(block_shift=12))
+    assert_same(res, oracle.topk(w))
+    assert list(res["ids"][1, :5]) == [0, 1, 2, 3, 4]
+
+
+def test_k_larger_than_objects_and_repeat_determinism():
+    w = synth.sets(3000, (4, 30), 600, 20, (1, 60), 1, config=20)
+    idx = runner.build_index(w)
+    for k in (1, 7, 1000, 1024):
+        qs = runner.compile_queries(idx, w)
+        a = runner.search(idx, qs, k).host()
+        b = runner.search(idx, qs, k).host()
+        torch.cuda.synchronize()
+        for key in a:
+            assert np.array_equal(a[key], b[key])
+        assert_same(a, oracle.topk(w, k=k))
+
+
+def test_two_streams_share_one_index():
+    w = synth.lsh(40_000, 32, 50, config=21)
+    idx = runner.build_index(w)
+    qs = runner.compile_queries(idx, w)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    o1 = runner.Outputs(w.n_queries, 50)
+    o2 = runner.Outputs(w.n_queries, 50)
+    torch.cuda.synchronize()
+    genie.genie_search(idx, qs, 50, o1.ids, o1.counts, o1.n_valid, stream=s1)
+    genie.genie_search(idx, qs, 50, o2.ids, o2.counts, o2.n_valid, stream=s2)
+    torch.cuda.synchronize()
+    a, b = o1.host(), o2.host()
+    for key in a:
+        assert np.array_equal(a[key], b[key])
+    assert_same(a, oracle.topk(w))
+
+
+def test_hash_table_overflow_falls_back_exactly():
+    w = synth.lsh(80_000, 24, 100, config=22)
+    stats = torch.zeros(8, dtype=torch.int64, device="cuda")
+    res, _, _ = run(w, chunk_shift=13, opts=genie.make_opts(block_shift=13, ht_slots=128,
+                                                             d_stats=stats))
+    assert_same(res, oracle.topk(w))
+    st = stats.cpu().numpy()
+    assert st[4] == w.n_queries * ((w.n_objects + 8191) >> 13)
+    assert st[2] > 0  # the Bitmap-Counter selection ran
+    assert st[5] == 0  # no inconsistent ids
+
+
+def test_seeded_gate_verify_and_rerun():
+    w = synth.lsh(60_000, 32, 30, config=23)
+    ref = oracle.topk(w)
+    idx = runner.build_index(w, 12)
+    qs = runner.compile_queries(idx, w)
+    rng = np.random.default_rng(5)
+    tk = ref["tk"].astype(np.int64)
+    for seeds in (np.maximum(tk, 1), tk + 1, np.ones_like(tk), tk + rng.integers(-3, 4, len(tk)),
+                  np.full_like(tk, 300)):
+        seeds = np.clip(seeds, 0, 1000).astype(np.uint32)
+        stats = torch.zeros(8, dtype=torch.int64, device="cuda")
+        d_seed = runner.to_dev(seeds)
+        out = runner.search(idx, qs, w.k, opts=genie.make_opts(d_seed=d_seed, block_shift=13,
+                                                               d_stats=stats))
+        torch.cuda.synchronize()
+        assert_same(out.host(), ref)
+        reruns = int(stats.cpu().numpy()[3])
+        expect = int(np.sum((seeds > 1) & (seeds > tk)))
+        assert reruns == expect
+
+
+# ---------------------------------------------------------------------------
+# errors are statuses, never faults
+# ---------------------------------------------------------------------------
+
+def _expect(status, fn, *a, **kw):
+    with pytest.raises(genie.GenieError) as e:
+        fn(*a, **kw)
+    assert e.value.status == status
+    assert genie.genie_last_error()
+
+
+def test_invalid_inputs_return_status():
+    d = runner.to_dev
+    off = d(np.array([0, 2, 3], np.uint32))
+    E = genie.GENIE_ERR_INVALID_ARG
+    _expect(E, genie.genie_build_index, off, d(np.array([0, 9, 1], np.uint32)), 2, 5)  # kw >= vocab
+    _expect(E, genie.genie_build_index, off, d(np.array([1, 1, 0], np.uint32)), 2, 5)  # repeat in set
+    _expect(E, genie.genie_build_index, d(np.array([0, 3, 2], np.uint32)),
+            d(np.array([0, 1, 2], np.uint32)), 2, 5)                                    # offsets
+    _expect(E, genie.genie_build_index, d(np.array([1, 2, 3], np.uint32)),
+            d(np.array([0, 1, 2], np.uint32)), 2, 5)                                    # off[0] != 0
+    _expect(E, genie.genie_build_index, off, d(np.array([0, 1, 2], np.uint32)), 2, 5, 30)  # shift
+    idx = genie.genie_build_index(off, d(np.array([0, 1, 2], np.uint32)), 2, 5)
+    _expect(E, genie.genie_make_queries, idx, d(np.array([0, 1], np.uint32)),
+            d(np.array([5], np.uint32)), 1)                                             # kw >= vocab
+    _expect(E, genie.genie_make_queries, idx, d(np.array([0, 2, 1], np.uint32)),
+            d(np.array([1, 2], np.uint32)), 2)                                          # offsets
+    long_q = np.zeros(5000, np.uint32)
+    big = genie.genie_build_index(d(np.arange(0, 5000 * 1 + 1, 1).astype(np.uint32)),
+                                  d(np.zeros(5000, np.uint32)), 5000, 1)
+    _expect(E, genie.genie_make_queries, big, d(np.array([0, 5000], np.uint32)), d(long_q), 1)
+    qs = genie.genie_make_queries(idx, d(np.array([0, 2], np.uint32)), d(np.array([1, 2], np.uint32)), 1)
+    o = runner.Outputs(1, 4)
+    _expect(E, genie.genie_search, idx, qs, 0, o.ids, o.counts, o.n_valid)
+    _expect(E, genie.genie_search, idx, qs, 2000, o.ids, o.counts, o.n_valid)
+    _expect(E, genie.genie_search, idx, qs, 4, o.ids, o.counts, o.n_valid,
+            d_k=d(np.array([5], np.uint32)))                                            # k_q > k
+    _expect(E, genie.genie_search, idx, qs, 4, o.ids, o.counts, o.n_valid,
+            opts=genie.make_opts(ht_slots=100))                                         # not pow2
+    other = genie.genie_build_index(off, d(np.array([0, 1, 2], np.uint32)), 2, 5)
+    _expect(E, genie.genie_search, other, qs, 4, o.ids, o.counts, o.n_valid)          # foreign
+    rel = genie.genie_build_index(d(np.array([0, 2], np.uint32)), d(np.array([1, 66], np.uint32)), 1, 128)
+    io = d(np.array([0, 1], np.uint32))
+    _expect(E, genie.genie_compile_ranges, rel, 64, io, d(np.array([0], np.uint32)),
+            d(np.array([5], np.int32)), d(np.array([4], np.int32)), 1)                 # lo > hi
+    _expect(E, genie.genie_compile_ranges, rel, 64, io, d(np.array([2], np.uint32)),
+            d(np.array([0], np.int32)), d(np.array([4], np.int32)), 1)                 # dim
+    # still usable afterwards
+    genie.genie_search(idx, qs, 4, o.ids, o.counts, o.n_valid)
+    torch.cuda.synchronize()
+    assert runner.u32(o.n_valid)[0] == 2
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads, in the launch configuration the benchmark uses
+# ---------------------------------------------------------------------------
+
+def _sampled(w, n_sample, seed):
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(w.n_queries, size=n_sample, replace=False))
+    return rows, oracle.topk(w.subset(rows))
+
+
+def test_full_lsh_1m_sampled():
+    w = synth.config(2)
+    res, idx, qs = run(w)
+    rows, ref = _sampled(w, 24, 0)
+    assert_same(res, ref, rows)
+    assert np.all(res["n_valid"] == 100)
+
+
+def test_full_zipf_4m_sampled():
+    w = synth.config(3)
+    res, idx, qs = run(w)
+    rows, ref = _sampled(w, 12, 1)
+    assert_same(res, ref, rows)
