@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["genie", "reference"], default="genie")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--queries", type=int, default=N_QUERIES,
+                    help="queries per batch (the workload is defined at 1024; smaller "
+                         "values are for profiling captures)")
     return ap.parse_args()
 
 
@@ -86,11 +89,11 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def workload(rank: int, world: int):
+def workload(rank: int, world: int, n_queries: int = N_QUERIES):
     import synth
-    w = synth.lsh(N_OBJECTS, N_QUERIES * world, K, config=2)
+    w = synth.lsh(N_OBJECTS, n_queries * world, K, config=2)
     if world > 1:
-        w = w.subset(np.arange(rank * N_QUERIES, (rank + 1) * N_QUERIES))
+        w = w.subset(np.arange(rank * n_queries, (rank + 1) * n_queries))
     return w
 
 
@@ -214,7 +217,7 @@ def run_genie(args, rank, world, local):
 
     _build.build()
     torch.cuda.set_device(local)
-    w = workload(rank, world)
+    w = workload(rank, world, args.queries)
     idx = runner.build_index(w)
     Q = w.n_queries
     d_q_off, d_q_kw = runner.to_dev(w.q_off), runner.to_dev(w.q_kw)
@@ -289,6 +292,16 @@ def run_genie(args, rank, world, local):
     h2d = (Q + 1) * 4 + int(w.q_off[-1]) * 4
     d2h = 2 * Q * K * 4 + Q * 4
 
+    # c-PQ counters from one more (untimed) pass
+    stats = torch.zeros(8, dtype=torch.int64, device="cuda")
+    qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
+    genie.genie_search(idx, qs, K, out.ids, out.counts, out.n_valid,
+                       opts=genie.make_opts(d_stats=stats), stream=stream)
+    st = stats.cpu().numpy()
+    cpq = {"gate_passes_per_posting": float(st[0]) / entries, "ht_inserts": int(st[1]),
+           "blocks": int(st[4]), "blocks_bitmap_fallback": int(st[2]), "bad_ids": int(st[5])}
+    del qs
+
     if rank != 0:
         return
     peak, peak_kind = measured_peaks()
@@ -311,6 +324,7 @@ def run_genie(args, rank, world, local):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
+        "cpq": cpq,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, BASELINE_SAMPLE)

@@ -23,17 +23,22 @@
 //    only grows (atomicMax), and a final pass sets AT_f = min{i >= AT :
 //    ZA[i] < k}.  For i >= AT_f, ZA[i] is exactly the number of objects with
 //    count >= i, so AT_f - 1 is the k-th count (Theorem 3.1).
-//  * Hash Table: keyed by object id, value = the count seen at insertion; an
-//    entry whose count is below AT - 1 may be overwritten (Sec. 3.3.2).  A
-//    pass at level val inserts only while ZA[val] < k before its own
-//    increment: once k objects reached val, an object at val can enter the
-//    top-k only through a later pass at a higher level or as a tie, and ties
-//    are read from the Bitmap Counter.  Every object with count >= AT_f
-//    keeps an entry with its exact count.
+//  * Hash Table: holds candidate object ids.  A Gate pass at level val is
+//    numbered z by its ZipperArray increment; the first k passes of a level
+//    (z < k) insert their object unless it is already present (a presence
+//    bit per object).  Counts live in the Bitmap Counter, so an entry whose
+//    object's count is below AT - 1 is expired and may be overwritten (Sec.
+//    3.3.2); the overwritten object loses its presence bit.  Every object
+//    with count >= AT_f passed level AT_f with z < k, so it was inserted and
+//    never expired.  The read-out is certified by its size: exactly
+//    ZA[AT_f] objects have count >= AT_f.  A read-out that fails the check
+//    (an insert that found no slot, or a lost race) is redone from the
+//    Bitmap Counter, so the result never depends on the hash table's luck.
 //  * Ties at the k-th count are filled in ascending object id from the
-//    Bitmap Counter (the paper breaks them randomly).  If the Hash Table ever
-//    runs out of slots, the block selects from the Bitmap Counter alone
-//    (histogram of counts, then the same ascending-id rule).
+//    Bitmap Counter (the paper breaks them randomly).
+//  * Gate passes of one warp that reach the same level share one
+//    ZipperArray atomic (warp match), which keeps the early levels, where
+//    thousands of objects pass at once, from serialising on one counter.
 #include <algorithm>
 #include <cstdio>
 
@@ -44,8 +49,6 @@ namespace genie {
 namespace {
 
 constexpr uint32_t kKwBatch = 512;  // query keywords staged in shared memory per round
-constexpr uint32_t kUnroll = 4;     // 16-byte loads in flight per lane
-constexpr uint32_t kTile = 32 * 4 * kUnroll;  // postings per warp tile (16-byte aligned)
 
 struct ScanArgs {
   const uint64_t* kw_off;
@@ -72,16 +75,24 @@ struct ScanArgs {
   unsigned long long* stats;
 };
 
-size_t scan_smem_bytes(uint32_t log2w, uint32_t block_shift, uint32_t ht_slots, uint32_t za_len) {
+constexpr uint32_t kMaxProbe = 32;   // hash-table probes before an insert gives up
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr uint32_t kMaxWarps = 32;   // per-warp Gate queues
+constexpr uint32_t kRing = 64;       // Gate candidates a warp can hold (power of two)
+
+size_t scan_smem_bytes(uint32_t log2w, uint32_t block_shift, uint32_t ht_slots, uint32_t za_len,
+                       uint32_t k) {
   size_t words = ((size_t)1 << block_shift) >> (5 - log2w);
-  return words * 4 + (size_t)ht_slots * 16 + (size_t)za_len * 4 + (3 * kKwBatch + 4) * 4;
+  size_t present = ((size_t)1 << block_shift) >> 5;
+  return words * 4 + present * 4 + (size_t)ht_slots * 4 + (size_t)dev::next_pow2(k) * 8 +
+         (size_t)za_len * 4 + (3 * kKwBatch + 4) * 4 + (size_t)kMaxWarps * kRing * 2 * 4;
 }
 
 __device__ __forceinline__ uint32_t vld(const uint32_t* p) { return *(const volatile uint32_t*)p; }
 
-// First `limit` lanes (ascending id) whose count equals `value` (or exceeds it
-// when GREATER) become result keys dst[0..); returns how many were written.
-template <int LOG2W, bool GREATER>
+// First `limit` lanes (ascending id) whose count equals `value` (or is at
+// least `value` when AT_LEAST) become result keys dst[0..); returns how many.
+template <int LOG2W, bool AT_LEAST>
 __device__ uint32_t collect_lanes(const uint32_t* bc, uint32_t nwords, uint32_t value,
                                   uint32_t limit, uint32_t obj_base, unsigned long long* dst,
                                   uint32_t* scratch) {
@@ -94,7 +105,7 @@ __device__ uint32_t collect_lanes(const uint32_t* bc, uint32_t nwords, uint32_t 
 #pragma unroll
     for (uint32_t l = 0; l < PER; ++l) {
       uint32_t v = (word >> (l * W)) & MASK;
-      m += GREATER ? (v > value) : (v == value);
+      m += AT_LEAST ? (v >= value) : (v == value);
     }
   }
   uint32_t total;
@@ -105,7 +116,7 @@ __device__ uint32_t collect_lanes(const uint32_t* bc, uint32_t nwords, uint32_t 
 #pragma unroll
       for (uint32_t l = 0; l < PER; ++l) {
         uint32_t v = (word >> (l * W)) & MASK;
-        if ((GREATER ? (v > value) : (v == value)) && pos < limit)
+        if ((AT_LEAST ? (v >= value) : (v == value)) && pos < limit)
           dst[pos++] = dev::result_key(v, obj_base + w * PER + l);
       }
     }
@@ -114,21 +125,119 @@ __device__ uint32_t collect_lanes(const uint32_t* bc, uint32_t nwords, uint32_t 
 }
 
 template <int LOG2W>
-__global__ void __launch_bounds__(1024, 1) scan_cpq_kernel(const ScanArgs A) {
+__device__ __forceinline__ uint32_t lane_count(const uint32_t* bc, uint32_t local) {
   constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, LPW = 5 - LOG2W, MASK = (1u << W) - 1u;
+  return (vld(&bc[local >> LPW]) >> ((local & (PER - 1)) << LOG2W)) & MASK;
+}
+
+// State the Gate touches, all in shared memory of one block.
+struct GateState {
+  uint32_t* za;       // ZipperArray, 1-based
+  uint32_t* present;  // one bit per object of the range: has a hash-table entry
+  uint32_t* ht;       // hash table of candidate ids
+  const uint32_t* bc; // Bitmap Counter
+  uint32_t* at;       // AuditThreshold
+  uint32_t* flags;    // [0] an insert found no slot, [1] a count above the bound
+};
+
+// Hash-table insert of a candidate id (once per object while it is flagged
+// present).  A slot is free when empty or when its object's exact count has
+// fallen below AT - 1 (Sec. 3.3.2); the evicted object loses its flag.
+template <int LOG2W>
+__device__ __noinline__ void ht_insert(const GateState g, uint32_t id, uint32_t obj_base,
+                                       uint32_t ht_mask, uint32_t ht_bits) {
+  uint32_t slot = ht_bits ? (id * 2654435761u) >> (32 - ht_bits) : 0u;
+  for (uint32_t probe = 0; probe < kMaxProbe; ++probe, slot = (slot + 1) & ht_mask) {
+    uint32_t e = vld(&g.ht[slot]);
+    for (;;) {
+      bool free_slot = e == kEmpty;
+      if (!free_slot) free_slot = lane_count<LOG2W>(g.bc, e - obj_base) + 1 < vld(g.at);
+      if (!free_slot) break;
+      uint32_t prev = atomicCAS(&g.ht[slot], e, id);
+      if (prev == e) {
+        if (e != kEmpty) {
+          uint32_t le = e - obj_base;
+          atomicAnd(&g.present[le >> 5], ~(1u << (le & 31)));
+        }
+        return;
+      }
+      e = prev;
+    }
+  }
+  g.flags[0] = 1;  // not placed: the read-out falls back to the Bitmap Counter
+}
+
+// The Gate of Algorithm 1 for n <= 32 candidates queued by one warp (lane l
+// takes entry head + l of the warp's ring).  Passes at the same level share one ZipperArray atomic;
+// z numbers a pass within its level; the first k passes of a level are
+// hash-table candidates; a full level advances AT.  Returns the passes of
+// this lane (0/1) and adds its inserts to *n_ins.
+template <int LOG2W>
+__device__ __noinline__ uint32_t gate_flush(const GateState g, const uint32_t* ring, uint32_t head,
+                                            uint32_t n, uint32_t kq, uint32_t B, uint32_t obj_base,
+                                            uint32_t ht_mask, uint32_t ht_bits, uint32_t* n_ins) {
+  const uint32_t lane = dev::lane_id();
+  __syncwarp();
+  const bool act = lane < n;
+  const uint32_t slot = (head + lane) & (kRing - 1);
+  const uint32_t id = act ? ring[slot] : 0u;
+  const uint32_t val = act ? ring[kRing + slot] : 0u;
+  __syncwarp();
+  if (act && val > B) g.flags[1] = 1;  // cannot happen with a valid bound
+  const bool pass = act && val >= vld(g.at) && val <= B;
+  const uint32_t m = __ballot_sync(0xFFFFFFFFu, pass);
+  if (!pass) return 0;
+  const uint32_t peers = __match_any_sync(m, val);
+  const uint32_t leader = __ffs(peers) - 1, n_peers = __popc(peers);
+  const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&g.za[val], n_peers);
+  base = __shfl_sync(peers, base, leader);
+  const uint32_t z = base + rank;
+  if (z < kq) {
+    const uint32_t local = id - obj_base;
+    const uint32_t w = local >> 5, b = 1u << (local & 31);
+    if (!(vld(&g.present[w]) & b) && !(atomicOr(&g.present[w], b) & b)) {
+      ++*n_ins;
+      ht_insert<LOG2W>(g, id, obj_base, ht_mask, ht_bits);
+    }
+  }
+  if (rank == n_peers - 1 && z + 1 >= kq) {  // level full: advance AT
+    uint32_t a = vld(g.at);
+    while (a <= B && vld(&g.za[a]) >= kq) {
+      atomicMax(g.at, a + 1);
+      ++a;
+    }
+  }
+  return 1;
+}
+
+// LOG2W: log2 of the counter width; U: 16-byte loads in flight per lane (a
+// warp tile is 128 * U postings); THREADS: block size.
+template <int LOG2W, int U, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) scan_cpq_kernel(const ScanArgs A) {
+  constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, LPW = 5 - LOG2W, MASK = (1u << W) - 1u;
+  constexpr uint32_t kUnroll = U, kTile = 32 * 4 * U;
   extern __shared__ uint4 smem_raw[];
-  __shared__ uint32_t s_at, s_overflow, s_err, s_n;
+  __shared__ uint32_t s_at, s_n, s_next;
+  __shared__ uint32_t s_flags[2];  // [0] hash table incomplete, [1] inconsistent input
   __shared__ uint32_t scratch[33];
   __shared__ unsigned long long scratch64[33];
 
+  // shared-memory layout: Bitmap Counter | presence bits | Hash Table | read-out
+  // buffer | ZipperArray | staged keyword segments
   const uint32_t nwords = (1u << A.block_shift) >> LPW;
+  const uint32_t npresent = (1u << A.block_shift) >> 5;
+  const uint32_t kpad = dev::next_pow2(A.k);
   uint32_t* bc = reinterpret_cast<uint32_t*>(smem_raw);
-  unsigned long long* ht = reinterpret_cast<unsigned long long*>(bc + nwords);
-  unsigned long long* cand = ht + A.ht_slots;
-  uint32_t* za = reinterpret_cast<uint32_t*>(cand + A.ht_slots);
+  uint32_t* present = bc + nwords;
+  uint32_t* ht = present + npresent;
+  unsigned long long* cand = reinterpret_cast<unsigned long long*>(ht + A.ht_slots);
+  uint32_t* za = reinterpret_cast<uint32_t*>(cand + kpad);
   uint32_t* seg_lo = za + A.za_len;
   uint32_t* seg_hi = seg_lo + kKwBatch;
   uint32_t* tile_pre = seg_hi + kKwBatch;
+  uint32_t* gq = tile_pre + kKwBatch + 4;  // [warp][id x kRing | val x kRing]
 
   const uint32_t tid = threadIdx.x, lane = dev::lane_id(), warp = dev::warp_id();
   const uint32_t nwarps = blockDim.x >> 5;
@@ -145,57 +254,24 @@ __global__ void __launch_bounds__(1024, 1) scan_cpq_kernel(const ScanArgs A) {
   {
     uint4* b4 = reinterpret_cast<uint4*>(bc);
     const uint4 z4 = make_uint4(0, 0, 0, 0);
-    for (uint32_t i = tid; i < (nwords >> 2); i += blockDim.x) b4[i] = z4;
-    for (uint32_t i = tid; i < A.ht_slots; i += blockDim.x) ht[i] = 0ull;
+    for (uint32_t i = tid; i < ((nwords + npresent) >> 2); i += blockDim.x) b4[i] = z4;
+    for (uint32_t i = tid; i < A.ht_slots; i += blockDim.x) ht[i] = kEmpty;
     for (uint32_t i = tid; i < B + 2; i += blockDim.x) za[i] = 0;
     if (tid == 0) {
       uint32_t s0 = A.seed ? A.seed[q] : 1u;
       s_at = max(1u, min(s0, B + 1));
-      s_overflow = 0;
-      s_err = 0;
+      s_flags[0] = 0;
+      s_flags[1] = 0;
     }
   }
   __syncthreads();
 
   uint32_t n_gate = 0, n_ins = 0;
 
-  // Gate of Algorithm 1 for one posting that raised object `id` to `val`.
-  auto gate = [&](uint32_t id, uint32_t val) {
-    if (val > B) {  // cannot happen with a valid bound; keeps shared memory safe
-      s_err = 1;
-      return;
-    }
-    ++n_gate;
-    uint32_t z = atomicAdd(&za[val], 1u);
-    if (z < kq) {
-      ++n_ins;
-      const unsigned long long mine = ((unsigned long long)val << 32) | id;
-      uint32_t slot = ht_bits ? (id * 2654435761u) >> (32 - ht_bits) : 0u;
-      bool done = false;
-      for (uint32_t probe = 0; probe < A.ht_slots && !done; ++probe, slot = (slot + 1) & ht_mask) {
-        unsigned long long e = *(volatile unsigned long long*)&ht[slot];
-        for (;;) {
-          uint32_t ecount = (uint32_t)(e >> 32), eid = (uint32_t)e;
-          if (ecount != 0 && eid == id) {
-            if (ecount >= val) { done = true; break; }
-          } else if (!(ecount == 0 || ecount + 1 < vld(&s_at))) {
-            break;  // a live entry of another object: probe on
-          }
-          unsigned long long prev = atomicCAS(&ht[slot], e, mine);
-          if (prev == e) { done = true; break; }
-          e = prev;
-        }
-      }
-      if (!done) s_overflow = 1;
-    }
-    if (z + 1 >= kq) {  // advance AT while its level is full
-      uint32_t a = vld(&s_at);
-      while (a <= B && vld(&za[a]) >= kq) {
-        atomicMax(&s_at, a + 1);
-        ++a;
-      }
-    }
-  };
+  uint32_t* ring = gq + warp * 2 * kRing;  // this warp's Gate queue
+  uint32_t qh = 0, qn = 0;                 // head and length
+  const uint32_t lmask = (1u << A.block_shift) - 1u;
+  const GateState gs{za, present, ht, bc, &s_at, s_flags};
 
   // ---- scan: all postings of the query's keywords inside this id range ---
   const uint32_t qa = A.q_off[q], qb = A.q_off[q + 1];
@@ -215,9 +291,11 @@ __global__ void __launch_bounds__(1024, 1) scan_cpq_kernel(const ScanArgs A) {
     uint32_t total_tiles;
     uint32_t pre = dev::block_exclusive_scan(ntiles, scratch, &total_tiles);
     if (tid < nk) tile_pre[tid] = pre;
+    if (tid == 0) s_next = nwarps;
     __syncthreads();
 
-    for (uint32_t t = warp; t < total_tiles; t += nwarps) {
+    // tiles are handed out dynamically: warps slowed by Gate work take fewer
+    for (uint32_t t = warp; t < total_tiles;) {
       uint32_t lo_j = 0, hi_j = nk;  // last j with tile_pre[j] <= t
       while (hi_j - lo_j > 1) {
         uint32_t mid = (lo_j + hi_j) >> 1;
@@ -232,37 +310,98 @@ __global__ void __launch_bounds__(1024, 1) scan_cpq_kernel(const ScanArgs A) {
         v[u] = idx < hi ? __ldg(reinterpret_cast<const uint4*>(A.post_ids + idx))
                         : make_uint4(0, 0, 0, 0);
       }
-      uint32_t old[4 * kUnroll];
-      uint32_t valid = 0;  // bit i: element i is a posting of this tile
+      // Bitmap Counter: one sub-word atomic add per posting (Algorithm 1,
+      // lines 1-2); val = the object's new count, 0 for slots outside the list
+      uint32_t val[4 * kUnroll];
+      if (start >= lo && start + kTile <= hi) {  // tile inside the list: no checks
 #pragma unroll
-      for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
-        const uint32_t u = i >> 2, e = i & 3;
-        const uint32_t pos = start + (u * 32 + lane) * 4 + e;
-        const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-        const uint32_t local = id - obj_base;
-        old[i] = 0;
-        if (pos >= lo && pos < hi) {
-          if (local < n_local) {
-            old[i] = atomicAdd(&bc[local >> LPW], 1u << ((local & (PER - 1)) << LOG2W));
-            valid |= 1u << i;
-          } else {
-            s_err = 1;  // an id outside this block's range: the index is inconsistent
+        for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
+          const uint32_t u = i >> 2, e = i & 3;
+          const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
+          const uint32_t local = (id - obj_base) & lmask;
+          const uint32_t sh = (local & (PER - 1)) << LOG2W;
+          val[i] = ((atomicAdd(&bc[local >> LPW], 1u << sh) >> sh) & MASK) + 1u;
+        }
+      } else {
+#pragma unroll
+        for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
+          const uint32_t u = i >> 2, e = i & 3;
+          const uint32_t pos = start + (u * 32 + lane) * 4 + e;
+          const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
+          const uint32_t local = id - obj_base;
+          val[i] = 0;
+          if (pos >= lo && pos < hi) {
+            if (local < n_local) {
+              const uint32_t sh = (local & (PER - 1)) << LOG2W;
+              val[i] = ((atomicAdd(&bc[local >> LPW], 1u << sh) >> sh) & MASK) + 1u;
+            } else {
+              s_flags[1] = 1;  // an id outside this block's range: the index is inconsistent
+            }
           }
         }
       }
-      uint32_t at_c = vld(&s_at);
+      // Gate (Algorithm 1, lines 3-7): postings whose new count reaches the
+      // (possibly stale) AuditThreshold join the warp's queue; the warp runs
+      // the Gate on 32 queued candidates at a time.
+      const uint32_t at_c = vld(&s_at);
+      uint32_t cm = 0;
 #pragma unroll
-      for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
-        if (!(valid & (1u << i))) continue;
-        const uint32_t u = i >> 2, e = i & 3;
-        const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-        const uint32_t local = id - obj_base;
-        const uint32_t val = ((old[i] >> ((local & (PER - 1)) << LOG2W)) & MASK) + 1u;
-        if (val >= at_c) {
-          at_c = vld(&s_at);
-          if (val >= at_c) gate(id, val);
+      for (uint32_t i = 0; i < 4 * kUnroll; ++i) cm |= (uint32_t)(val[i] >= at_c) << i;
+      const uint32_t nc = __popc(cm);
+      const uint32_t incl = dev::warp_inclusive_scan(nc);
+      const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      if (total) {
+        if (qn + total > kRing) {  // make room: run the Gate on the backlog
+          while (qn) {
+            const uint32_t f = min(qn, 32u);
+            n_gate += gate_flush<LOG2W>(gs, ring, qh, f, kq, B, obj_base, ht_mask, ht_bits, &n_ins);
+            qh += f;
+            qn -= f;
+          }
+        }
+        if (total <= kRing) {
+          uint32_t p = qh + qn + incl - nc;
+#pragma unroll
+          for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
+            if ((cm >> i) & 1u) {
+              const uint32_t u = i >> 2, e = i & 3;
+              ring[p & (kRing - 1)] = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
+              ring[kRing + (p & (kRing - 1))] = val[i];
+              ++p;
+            }
+          }
+          qn += total;
+          while (qn >= 32) {
+            n_gate += gate_flush<LOG2W>(gs, ring, qh, 32, kq, B, obj_base, ht_mask, ht_bits, &n_ins);
+            qh += 32;
+            qn -= 32;
+          }
+        } else {  // a burst larger than the queue: one element slot at a time
+#pragma unroll
+          for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
+            const bool c = (cm >> i) & 1u;
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, c);
+            if (m == 0) continue;
+            if (c) {
+              const uint32_t u = i >> 2, e = i & 3;
+              const uint32_t p = (qh + __popc(m & ((1u << lane) - 1u))) & (kRing - 1);
+              ring[p] = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
+              ring[kRing + p] = val[i];
+            }
+            n_gate += gate_flush<LOG2W>(gs, ring, qh, __popc(m), kq, B, obj_base, ht_mask, ht_bits,
+                                        &n_ins);
+          }
         }
       }
+      uint32_t nt = 0;
+      if (lane == 0) nt = atomicAdd(&s_next, 1u);
+      t = __shfl_sync(0xFFFFFFFFu, nt, 0);
+    }
+    while (qn) {
+      const uint32_t f = min(qn, 32u);
+      n_gate += gate_flush<LOG2W>(gs, ring, qh, f, kq, B, obj_base, ht_mask, ht_bits, &n_ins);
+      qh += f;
+      qn -= f;
     }
     __syncthreads();
   }
@@ -278,67 +417,37 @@ __global__ void __launch_bounds__(1024, 1) scan_cpq_kernel(const ScanArgs A) {
   const uint32_t at_f = s_at;
   const uint32_t nwords_local = (n_local + PER - 1) / PER;
   unsigned long long* out = A.cand + ((unsigned long long)qi * A.n_groups + g) * A.k;
-  uint32_t n_hi, tie_v;
-  if (!s_overflow) {
-    // Theorem 3.1: the objects with count >= AT_f are in the HT (exact count
-    // re-read from the Bitmap Counter; duplicates of one id collapse below)
-    for (uint32_t i = tid; i < A.ht_slots; i += blockDim.x) {
-      unsigned long long e = ht[i];
-      uint32_t c = (uint32_t)(e >> 32);
-      if (c != 0 && c >= at_f) {
-        uint32_t id = (uint32_t)e, local = id - obj_base;
-        uint32_t exact = (bc[local >> LPW] >> ((local & (PER - 1)) << LOG2W)) & MASK;
-        cand[atomicAdd(&s_n, 1u)] = dev::result_key(exact, id);
-      }
+  // Theorem 3.1: the objects with count >= AT_f are candidates in the HT; their
+  // number is exactly ZA[AT_f] (every object at or above AT_f passed that level
+  // through the Gate), which certifies the read-out.
+  const uint32_t want = za[at_f];
+  for (uint32_t i = tid; i < A.ht_slots; i += blockDim.x) {
+    uint32_t id = ht[i];
+    if (id == kEmpty) continue;
+    uint32_t c = lane_count<LOG2W>(bc, id - obj_base);
+    if (c >= at_f) {
+      uint32_t p = atomicAdd(&s_n, 1u);
+      if (p < kpad) cand[p] = dev::result_key(c, id);
     }
-    __syncthreads();
-    const uint32_t n = s_n, n2 = dev::next_pow2(max(n, 1u));
-    for (uint32_t i = n + tid; i < n2; i += blockDim.x) cand[i] = 0ull;
-    __syncthreads();
-    dev::bitonic_sort_desc(cand, n2);
-    if (tid == 0) {
-      uint32_t w = 0;
-      for (uint32_t i = 0; i < n; ++i)
-        if (w == 0 || cand[i] != cand[w - 1]) cand[w++] = cand[i];
-      s_n = min(w, kq);
-    }
-    __syncthreads();
-    n_hi = s_n;
-    tie_v = at_f - 1;  // 0 when AT_f = 1: no ties to add
-  } else {
-    // Bitmap-Counter selection: histogram of counts in ZA's storage
-    for (uint32_t i = tid; i < B + 2; i += blockDim.x) za[i] = 0;
-    __syncthreads();
-    for (uint32_t w = tid; w < nwords_local; w += blockDim.x) {
-      uint32_t word = bc[w];
-#pragma unroll
-      for (uint32_t l = 0; l < PER; ++l) {
-        uint32_t v = (word >> (l * W)) & MASK;
-        if (v) atomicAdd(&za[min(v, B + 1)], 1u);
-      }
-    }
-    __syncthreads();
-    if (tid == 0) {
-      uint32_t cum = 0, t = 1;
-      for (uint32_t v = B + 1; v >= 1; --v) {
-        if (cum + za[v] >= kq) { t = v; break; }
-        cum += za[v];
-      }
-      s_n = t;
-    }
-    __syncthreads();
-    tie_v = s_n;
-    n_hi = collect_lanes<LOG2W, true>(bc, nwords_local, tie_v, kq, obj_base, cand, scratch);
-    __syncthreads();
+  }
+  __syncthreads();
+  uint32_t n_hi = s_n;
+  const bool certified = !s_flags[0] && n_hi == want && n_hi < kq;
+  if (!certified)  // Bitmap-Counter selection of the same set
+    n_hi = collect_lanes<LOG2W, true>(bc, nwords_local, at_f, kq, obj_base, cand, scratch);
+  __syncthreads();
+  {
     const uint32_t n2 = dev::next_pow2(max(n_hi, 1u));
     for (uint32_t i = n_hi + tid; i < n2; i += blockDim.x) cand[i] = 0ull;
     __syncthreads();
     dev::bitonic_sort_desc(cand, n2);
   }
   for (uint32_t i = tid; i < n_hi; i += blockDim.x) out[i] = cand[i];
+  // ties at the k-th count, ascending id, from the Bitmap Counter
   uint32_t n_tie = 0;
-  if (tie_v >= 1 && n_hi < kq)
-    n_tie = collect_lanes<LOG2W, false>(bc, nwords_local, tie_v, kq - n_hi, obj_base, out + n_hi, scratch);
+  if (at_f >= 2 && n_hi < kq)
+    n_tie = collect_lanes<LOG2W, false>(bc, nwords_local, at_f - 1, kq - n_hi, obj_base,
+                                        out + n_hi, scratch);
   for (uint32_t i = n_hi + n_tie + tid; i < kq; i += blockDim.x) out[i] = 0ull;
 
   if (A.chunk_at && tid == 0) A.chunk_at[(unsigned long long)qi * A.n_groups + g] = at_f;
@@ -348,9 +457,9 @@ __global__ void __launch_bounds__(1024, 1) scan_cpq_kernel(const ScanArgs A) {
     if (tid == 0) {
       atomicAdd(&A.stats[0], gsum);
       atomicAdd(&A.stats[1], isum);
-      if (s_overflow) atomicAdd(&A.stats[2], 1ull);
+      if (!certified) atomicAdd(&A.stats[2], 1ull);
       atomicAdd(&A.stats[4], 1ull);
-      if (s_err) atomicAdd(&A.stats[5], 1ull);
+      if (s_flags[1]) atomicAdd(&A.stats[5], 1ull);
     }
   }
 }
@@ -478,6 +587,7 @@ __global__ void check_k_kernel(uint32_t n_queries, uint32_t k, const uint32_t* _
 
 struct Plan {
   uint32_t log2w;
+  uint32_t unroll;
   uint32_t block_shift;
   uint32_t n_groups;
   uint32_t ht_slots;
@@ -498,15 +608,18 @@ genie_status make_plan(const genie_index* idx, const genie_queries* qs, uint32_t
   shift = std::max(shift, idx->chunk_shift);
   p->block_shift = shift;
   p->n_groups = (uint32_t)(((uint64_t)idx->n_objects + (1ull << shift) - 1) >> shift);
-  uint32_t slots = (o && o->ht_slots) ? o->ht_slots : std::max(64u, dev::next_pow2(4 * k));
+  uint32_t slots = (o && o->ht_slots) ? o->ht_slots : std::max(256u, dev::next_pow2(8 * k));
   if (slots & (slots - 1)) return fail(GENIE_ERR_INVALID_ARG, "genie_search: ht_slots must be a power of two");
-  if (slots < k) return fail(GENIE_ERR_INVALID_ARG, "genie_search: ht_slots must be >= k");
+  if (slots < 32) return fail(GENIE_ERR_INVALID_ARG, "genie_search: ht_slots must be >= 32");
   p->ht_slots = slots;
   p->threads = (o && o->threads) ? o->threads : 1024u;
-  if (p->threads % 32 || p->threads < kKwBatch || p->threads > 1024)
-    return fail(GENIE_ERR_INVALID_ARG, "genie_search: threads must be a multiple of 32 in 512..1024");
+  if (p->threads != 512 && p->threads != 1024)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search: threads must be 512 or 1024");
+  p->unroll = (o && o->unroll) ? o->unroll : (p->threads == 512 ? 4u : 2u);
+  if (p->threads == 512 ? (p->unroll != 4 && p->unroll != 8) : (p->unroll != 2 && p->unroll != 4))
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search: unroll must be 2 or 4 (1024 threads), 4 or 8 (512)");
   p->za_len = B + 2;
-  p->smem = scan_smem_bytes(p->log2w, shift, slots, p->za_len);
+  p->smem = scan_smem_bytes(p->log2w, shift, slots, p->za_len, k);
   int dev = 0, max_smem = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -515,14 +628,27 @@ genie_status make_plan(const genie_index* idx, const genie_queries* qs, uint32_t
   return GENIE_OK;
 }
 
-template <int LOG2W>
+template <int LOG2W, int U, int THREADS>
 cudaError_t launch_scan(const ScanArgs& a, const Plan& p, cudaStream_t s) {
-  auto kern = scan_cpq_kernel<LOG2W>;
+  auto kern = scan_cpq_kernel<LOG2W, U, THREADS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
   if (e != cudaSuccess) return e;
   const uint64_t blocks = (uint64_t)a.n_sel * a.n_groups;
   kern<<<(uint32_t)blocks, p.threads, p.smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int LOG2W>
+cudaError_t dispatch_width(const ScanArgs& a, const Plan& p, cudaStream_t s) {
+  if (p.threads == 512) return p.unroll == 8 ? launch_scan<LOG2W, 8, 512>(a, p, s)
+                                             : launch_scan<LOG2W, 4, 512>(a, p, s);
+  return p.unroll == 4 ? launch_scan<LOG2W, 4, 1024>(a, p, s) : launch_scan<LOG2W, 2, 1024>(a, p, s);
+}
+
+cudaError_t dispatch_scan(const ScanArgs& a, const Plan& p, cudaStream_t s) {
+  return p.log2w == 2 ? dispatch_width<2>(a, p, s)
+       : p.log2w == 3 ? dispatch_width<3>(a, p, s)
+                      : dispatch_width<4>(a, p, s);
 }
 
 cudaError_t run_pass(const genie_index* idx, const genie_queries* qs, uint32_t k, const uint32_t* d_k,
@@ -554,9 +680,7 @@ cudaError_t run_pass(const genie_index* idx, const genie_queries* qs, uint32_t k
   a.stats = o ? o->d_stats : nullptr;
   const bool timed = o && !sel && o->scan_event_begin && o->scan_event_end;
   if (timed) cudaEventRecord((cudaEvent_t)o->scan_event_begin, s);
-  cudaError_t e = p.log2w == 2 ? launch_scan<2>(a, p, s)
-                : p.log2w == 3 ? launch_scan<3>(a, p, s)
-                               : launch_scan<4>(a, p, s);
+  cudaError_t e = dispatch_scan(a, p, s);
   if (e != cudaSuccess) return e;
   if (timed) cudaEventRecord((cudaEvent_t)o->scan_event_end, s);
   MergeArgs m;

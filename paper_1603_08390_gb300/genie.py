@@ -54,6 +54,7 @@ class QueriesInfo(ctypes.Structure):
 class SearchOpts(ctypes.Structure):
     _fields_ = [("d_seed", ctypes.c_void_p), ("block_shift", ctypes.c_uint32),
                 ("threads", ctypes.c_uint32), ("ht_slots", ctypes.c_uint32),
+                ("unroll", ctypes.c_uint32),
                 ("d_chunk_at", ctypes.c_void_p), ("d_stats", ctypes.c_void_p),
                 ("h_blocks_per_query", ctypes.POINTER(ctypes.c_uint32)),
                 ("scan_event_begin", ctypes.c_void_p), ("scan_event_end", ctypes.c_void_p)]
@@ -222,12 +223,13 @@ def genie_queries_export(queries: Queries, d_bound=None, d_entries=None, d_featu
 
 
 def make_opts(d_seed=None, block_shift: int = 0, threads: int = 0, ht_slots: int = 0,
-              d_chunk_at=None, d_stats=None, scan_events=None) -> SearchOpts:
+              d_chunk_at=None, d_stats=None, scan_events=None, unroll: int = 0) -> SearchOpts:
     o = SearchOpts()
     o.d_seed = _ptr(d_seed)
     o.block_shift = block_shift
     o.threads = threads
     o.ht_slots = ht_slots
+    o.unroll = unroll
     o.d_chunk_at = _ptr(d_chunk_at)
     o.d_stats = _ptr(d_stats)
     o._blocks = ctypes.c_uint32(0)

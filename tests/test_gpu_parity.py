@@ -215,7 +215,7 @@ def test_two_streams_share_one_index():
 def test_hash_table_overflow_falls_back_exactly():
     w = synth.lsh(80_000, 24, 100, config=22)
     stats = torch.zeros(8, dtype=torch.int64, device="cuda")
-    res, _, _ = run(w, chunk_shift=13, opts=genie.make_opts(block_shift=13, ht_slots=128,
+    res, _, _ = run(w, chunk_shift=13, opts=genie.make_opts(block_shift=13, ht_slots=32,
                                                              d_stats=stats))
     assert_same(res, oracle.topk(w))
     st = stats.cpu().numpy()
