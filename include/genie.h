@@ -235,6 +235,38 @@ genie_status genie_search(const genie_index* index, const genie_queries* queries
                           const uint32_t* d_k, const genie_search_opts* opts, uint32_t* d_ids,
                           uint32_t* d_counts, uint32_t* d_n_valid, genie_stream stream);
 
+/*
+ * genie_search without any device allocation.  The paper has no counterpart;
+ * this entry point exists for callers that cannot allocate device memory while
+ * they answer queries: a process under a hard memory budget, a host program
+ * whose framework owns every device allocation through its own pool, or a
+ * latency-critical loop that must not pay for (or fail on) an allocation.
+ *
+ * Same arguments, results and errors as genie_search, with these differences:
+ *   - Scratch lives in one fixed 16 MiB device array inside the library
+ *     (held on every GPU that loads the library until the process exits).
+ *     A call needs n_queries x (object ranges per query) x k x 8 bytes of it;
+ *     larger calls return GENIE_ERR_CAPACITY with the sizes in the message
+ *     (split the batch, or use genie_search).  Object ranges per query =
+ *     ceil(n_objects / 2^16) for 16-bit counters (B_q > 255),
+ *     ceil(n_objects / 2^17) for 8-bit, ceil(n_objects / 2^18) for 4-bit,
+ *     unless opts->block_shift sets it.
+ *   - opts->d_seed must be NULL (seeded searches rerun queries and need
+ *     genie_search); opts is otherwise honoured.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, once per device, with that device current).
+ *     Make that first call before any stream capture on that device.
+ *   - Every call uses the same array.  Calls whose work overlaps on the GPU
+ *     (different streams, or different host threads) race on it; serialise
+ *     them, e.g. by issuing them on one stream.
+ * The function itself calls no cudaMalloc, cudaFree or other allocating
+ * routine.  With d_k it synchronises `stream` once to validate the per-query k.
+ */
+genie_status genie_search_noalloc(const genie_index* index, const genie_queries* queries,
+                                  uint32_t k, const uint32_t* d_k, const genie_search_opts* opts,
+                                  uint32_t* d_ids, uint32_t* d_counts, uint32_t* d_n_valid,
+                                  genie_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -41,6 +41,8 @@
 //    thousands of objects pass at once, from serialising on one counter.
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
+#include <string>
 
 #include "device_util.cuh"
 #include "internal.h"
@@ -766,5 +768,101 @@ extern "C" genie_status genie_search(const genie_index* index, const genie_queri
   }
   release();
   if (e != cudaSuccess) return fail_cuda(e, "genie_search");
+  return GENIE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// genie_search_noalloc: the same search with its scratch in a fixed device array
+// ---------------------------------------------------------------------------
+//
+// For callers that must not allocate device memory while they answer
+// queries: code that runs under a hard memory budget, shares the GPU with a
+// framework that owns every allocation through its own pool, or cannot take
+// an allocation's latency or failure on the query path.  The per-range
+// candidate lists and a status word live in one file-scope device array of
+// fixed size, which every GPU that loads this library holds until the
+// process exits.
+
+namespace genie {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB
+constexpr size_t kNoAllocStatusBytes = 256;                // after the candidate lists
+
+// Host code may not pass this name to a kernel: on the host it stands for a
+// shadow symbol, not a device address.  Its device address is looked up per
+// device (scratch_address) and passed instead.
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device; looked up once
+// per device (the first call on a device), with that device current.
+genie_status scratch_address(void** out) {
+  int dev = 0;
+  GENIE_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search_noalloc: device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail_cuda(e, "genie_search_noalloc: cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return GENIE_OK;
+}
+
+}  // namespace
+}  // namespace genie
+
+extern "C" genie_status genie_search_noalloc(const genie_index* index, const genie_queries* queries,
+                                             uint32_t k, const uint32_t* d_k,
+                                             const genie_search_opts* opts, uint32_t* d_ids,
+                                             uint32_t* d_counts, uint32_t* d_n_valid,
+                                             genie_stream stream) {
+  if (!index || !queries || !d_ids || !d_counts || !d_n_valid)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search_noalloc: NULL argument");
+  if (queries->index != index)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search_noalloc: queries were compiled for another index");
+  if (k == 0 || k > GENIE_MAX_K)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search_noalloc: k must be in 1..GENIE_MAX_K");
+  if (opts && opts->d_seed)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search_noalloc: seeded searches need genie_search");
+  cudaStream_t s = as_stream(stream);
+  Plan p;
+  genie_status st = make_plan(index, queries, k, opts, &p);
+  if (st != GENIE_OK) return st;
+  if (opts && opts->h_blocks_per_query) *opts->h_blocks_per_query = p.n_groups;
+  const uint64_t cand_bytes = (uint64_t)queries->n_queries * p.n_groups * k * 8;
+  if (cand_bytes > kNoAllocScratchBytes - kNoAllocStatusBytes)
+    return fail(GENIE_ERR_CAPACITY,
+                "genie_search_noalloc: queries x object ranges x k x 8 bytes = " +
+                    std::to_string(cand_bytes) + " exceeds the fixed scratch of " +
+                    std::to_string(kNoAllocScratchBytes - kNoAllocStatusBytes) +
+                    " bytes; use fewer queries per call or genie_search");
+  void* base = nullptr;
+  st = scratch_address(&base);
+  if (st != GENIE_OK) return st;
+  unsigned long long* cand = static_cast<unsigned long long*>(base);
+  uint32_t* status = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(base) +
+                                                 kNoAllocScratchBytes - kNoAllocStatusBytes);
+  const uint32_t Q = queries->n_queries;
+  if (d_k) {  // the status word keeps the last call's value: clear it first
+    uint32_t bad = 0;
+    GENIE_CUDA_TRY(cudaMemsetAsync(status, 0, 4, s));
+    check_k_kernel<<<std::min<uint32_t>((Q + 255) / 256, 1024u), 256, 0, s>>>(Q, k, d_k, status);
+    GENIE_CUDA_TRY(cudaMemcpyAsync(&bad, status, 4, cudaMemcpyDeviceToHost, s));
+    GENIE_CUDA_TRY(cudaStreamSynchronize(s));
+    if (bad) return fail(GENIE_ERR_INVALID_ARG, "genie_search_noalloc: a per-query k is 0 or larger than k");
+  }
+  // the scan kernel writes every candidate slot the merge reads, so the
+  // candidate lists need no clearing between calls
+  cudaError_t e = run_pass(index, queries, k, d_k, nullptr, nullptr, Q, p, opts, cand, d_ids,
+                           d_counts, d_n_valid, s);
+  if (e != cudaSuccess) return fail_cuda(e, "genie_search_noalloc");
   return GENIE_OK;
 }

@@ -30,6 +30,7 @@ EXPORTED = (
     "genie_last_error", "genie_version", "genie_build_index", "genie_index_destroy",
     "genie_index_get_info", "genie_index_export", "genie_make_queries", "genie_compile_ranges",
     "genie_queries_destroy", "genie_queries_get_info", "genie_queries_export", "genie_search",
+    "genie_search_noalloc",
 )
 
 
@@ -99,6 +100,8 @@ def load(path: Optional[str] = None):
         lib.genie_queries_export.restype = st
         lib.genie_search.argtypes = [vp, vp, u32, vp, ctypes.POINTER(SearchOpts), vp, vp, vp, vp]
         lib.genie_search.restype = st
+        lib.genie_search_noalloc.argtypes = lib.genie_search.argtypes
+        lib.genie_search_noalloc.restype = st
         _LIB = lib
         return lib
 
@@ -247,3 +250,14 @@ def genie_search(index: Index, queries: Queries, k: int, d_ids, d_counts, d_n_va
     _check(lib.genie_search(index.handle, queries.handle, k, _ptr(d_k),
                             ctypes.byref(opts) if opts is not None else None, _ptr(d_ids),
                             _ptr(d_counts), _ptr(d_n_valid), _stream(stream)), lib)
+
+
+def genie_search_noalloc(index: Index, queries: Queries, k: int, d_ids, d_counts, d_n_valid,
+                         d_k=None, opts: Optional[SearchOpts] = None, stream=None) -> None:
+    """genie_search with its scratch in the library's fixed device array: for
+    callers that cannot allocate device memory while answering queries (see
+    include/genie.h for the size limit and the sharing rules)."""
+    lib = load()
+    _check(lib.genie_search_noalloc(index.handle, queries.handle, k, _ptr(d_k),
+                                    ctypes.byref(opts) if opts is not None else None, _ptr(d_ids),
+                                    _ptr(d_counts), _ptr(d_n_valid), _stream(stream)), lib)
