@@ -235,6 +235,57 @@ genie_status genie_search(const genie_index* index, const genie_queries* queries
                           const uint32_t* d_k, const genie_search_opts* opts, uint32_t* d_ids,
                           uint32_t* d_counts, uint32_t* d_n_valid, genie_stream stream);
 
+/* ------------------------------------------------------------------------ */
+/* k-th-count predictor: a learned AuditThreshold seed (not in the paper)    */
+/* ------------------------------------------------------------------------ */
+/*
+ * A 64-128-1 ReLU network predicts each query's k-th match count from the
+ * query's feature histogram (genie_queries_export).  Its prediction seeds
+ * the AuditThreshold of Algorithm 1 through genie_search_opts.d_seed; the
+ * seeded search stays exact (it verifies every query and reruns the ones it
+ * cannot certify), so the network only changes how much Gate work a search
+ * does.  Parameters theta = [W1 (128 x 64, row-major: W1[j*64 + i]) | b1
+ * (128) | w2 (128) | b2 (1)], genie_mlp_num_params() floats.  The library
+ * keeps float32 masters (and Adam state) and bfloat16 copies of W1 and w2;
+ * forward and backward use the bfloat16 weights with float32 accumulation:
+ *   y = w2 . relu(W1 x + b1) + b2,  loss = mean 0.5 (y - t)^2.
+ */
+typedef struct genie_mlp genie_mlp;
+
+uint32_t genie_mlp_num_params(void);
+
+/* New network, He-uniform weights from `seed`, zero biases and Adam state. */
+genie_status genie_mlp_create(uint64_t seed, genie_stream stream, genie_mlp** out);
+void genie_mlp_destroy(genie_mlp* mlp);
+
+/* Copy float32 parameters in (d_theta, device) / out; set also resets Adam. */
+genie_status genie_mlp_set_params(genie_mlp* mlp, const float* d_theta, genie_stream stream);
+genie_status genie_mlp_get_params(const genie_mlp* mlp, float* d_theta, genie_stream stream);
+
+/* d_y[n] = network(d_x[n*64 ..]) for n samples (device arrays). */
+genie_status genie_mlp_forward(const genie_mlp* mlp, const float* d_x, uint32_t n, float* d_y,
+                               genie_stream stream);
+
+/* Gradient of the mean loss over the n samples (d_x, targets d_t) into the
+ * network's gradient buffer; if d_grad != NULL also copies it out there
+ * ([num_params] floats, then the summed squared error). */
+genie_status genie_mlp_gradients(genie_mlp* mlp, const float* d_x, const float* d_t, uint32_t n,
+                                 float* d_grad, genie_stream stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the last gradients. */
+genie_status genie_mlp_adam_step(genie_mlp* mlp, float lr, genie_stream stream);
+
+/* `epochs` passes of mini-batch Adam over (d_x, d_t) in order; h_loss (may be
+ * NULL) receives the final mean loss over all n samples (synchronises). */
+genie_status genie_mlp_train(genie_mlp* mlp, const float* d_x, const float* d_t, uint32_t n,
+                             uint32_t epochs, uint32_t batch, float lr, float* h_loss,
+                             genie_stream stream);
+
+/* AuditThreshold seeds for compiled queries:
+ * d_seed[q] = clamp(floor(y_q - margin), 1, B_q + 1), y_q = network(features of q). */
+genie_status genie_mlp_seeds(genie_mlp* mlp, const genie_queries* queries, float margin,
+                             uint32_t* d_seed, genie_stream stream);
+
 /*
  * genie_search without any device allocation.  The paper has no counterpart;
  * this entry point exists for callers that cannot allocate device memory while

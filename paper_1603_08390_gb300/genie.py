@@ -30,7 +30,9 @@ EXPORTED = (
     "genie_last_error", "genie_version", "genie_build_index", "genie_index_destroy",
     "genie_index_get_info", "genie_index_export", "genie_make_queries", "genie_compile_ranges",
     "genie_queries_destroy", "genie_queries_get_info", "genie_queries_export", "genie_search",
-    "genie_search_noalloc",
+    "genie_search_noalloc", "genie_mlp_num_params", "genie_mlp_create", "genie_mlp_destroy",
+    "genie_mlp_set_params", "genie_mlp_get_params", "genie_mlp_forward", "genie_mlp_gradients",
+    "genie_mlp_adam_step", "genie_mlp_train", "genie_mlp_seeds",
 )
 
 
@@ -102,6 +104,23 @@ def load(path: Optional[str] = None):
         lib.genie_search.restype = st
         lib.genie_search_noalloc.argtypes = lib.genie_search.argtypes
         lib.genie_search_noalloc.restype = st
+        f32 = ctypes.c_float
+        lib.genie_mlp_num_params.restype = u32
+        lib.genie_mlp_num_params.argtypes = []
+        lib.genie_mlp_create.argtypes = [u64, vp, ctypes.POINTER(vp)]
+        lib.genie_mlp_destroy.argtypes = [vp]
+        lib.genie_mlp_destroy.restype = None
+        lib.genie_mlp_set_params.argtypes = [vp, vp, vp]
+        lib.genie_mlp_get_params.argtypes = [vp, vp, vp]
+        lib.genie_mlp_forward.argtypes = [vp, vp, u32, vp, vp]
+        lib.genie_mlp_gradients.argtypes = [vp, vp, vp, u32, vp, vp]
+        lib.genie_mlp_adam_step.argtypes = [vp, f32, vp]
+        lib.genie_mlp_train.argtypes = [vp, vp, vp, u32, u32, u32, f32, ctypes.POINTER(f32), vp]
+        lib.genie_mlp_seeds.argtypes = [vp, vp, f32, vp, vp]
+        for name in ("genie_mlp_create", "genie_mlp_set_params", "genie_mlp_get_params",
+                     "genie_mlp_forward", "genie_mlp_gradients", "genie_mlp_adam_step",
+                     "genie_mlp_train", "genie_mlp_seeds"):
+            getattr(lib, name).restype = st
         _LIB = lib
         return lib
 
@@ -261,3 +280,51 @@ def genie_search_noalloc(index: Index, queries: Queries, k: int, d_ids, d_counts
     _check(lib.genie_search_noalloc(index.handle, queries.handle, k, _ptr(d_k),
                                     ctypes.byref(opts) if opts is not None else None, _ptr(d_ids),
                                     _ptr(d_counts), _ptr(d_n_valid), _stream(stream)), lib)
+
+
+class MLP:
+    """Owning wrapper of a ``genie_mlp*`` (the k-th-count predictor)."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        lib = load()
+        out = ctypes.c_void_p()
+        _check(lib.genie_mlp_create(seed, _stream(stream), ctypes.byref(out)), lib)
+        self.handle = out.value
+        self.n_params = lib.genie_mlp_num_params()
+
+    def close(self):
+        if self.handle:
+            load().genie_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, d_theta, stream=None):
+        _check(load().genie_mlp_set_params(self.handle, _ptr(d_theta), _stream(stream)), load())
+
+    def get_params(self, d_theta, stream=None):
+        _check(load().genie_mlp_get_params(self.handle, _ptr(d_theta), _stream(stream)), load())
+
+    def forward(self, d_x, n: int, d_y, stream=None):
+        _check(load().genie_mlp_forward(self.handle, _ptr(d_x), n, _ptr(d_y), _stream(stream)), load())
+
+    def gradients(self, d_x, d_t, n: int, d_grad=None, stream=None):
+        _check(load().genie_mlp_gradients(self.handle, _ptr(d_x), _ptr(d_t), n, _ptr(d_grad),
+                                          _stream(stream)), load())
+
+    def adam_step(self, lr: float, stream=None):
+        _check(load().genie_mlp_adam_step(self.handle, lr, _stream(stream)), load())
+
+    def train(self, d_x, d_t, n: int, epochs: int, batch: int, lr: float, stream=None) -> float:
+        loss = ctypes.c_float(0.0)
+        _check(load().genie_mlp_train(self.handle, _ptr(d_x), _ptr(d_t), n, epochs, batch, lr,
+                                      ctypes.byref(loss), _stream(stream)), load())
+        return float(loss.value)
+
+    def seeds(self, queries: Queries, margin: float, d_seed, stream=None):
+        _check(load().genie_mlp_seeds(self.handle, queries.handle, margin, _ptr(d_seed),
+                                      _stream(stream)), load())
