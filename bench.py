@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["genie", "reference"], default="genie")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["lsh1m", "lsh4m-learned"], default="lsh1m",
+                    help="lsh1m: the headline batch; lsh4m-learned: plain vs learned-seed "
+                         "search on 4M objects / 4096 queries (k=100)")
     ap.add_argument("--queries", type=int, default=N_QUERIES,
                     help="queries per batch (the workload is defined at 1024; smaller "
                          "values are for profiling captures)")
@@ -331,11 +334,104 @@ def run_genie(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def timed_steps(step, steps, stream):
+    """CUDA-event time of `steps` calls of step(); returns (total ms, per-step ms)."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for i in range(steps):
+        step()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    return ev[0].elapsed_time(ev[-1]), per
+
+
+def run_learned(args, rank, world, local):
+    """Plain vs learned-seed search on the 4M-object LSH workload."""
+    import torch
+    import synth
+    from paper_1603_08390_gb300 import _build, genie, learned, runner
+
+    _build.build()
+    torch.cuda.set_device(local)
+    k = 100
+    w = synth.config(4)
+    idx = runner.build_index(w)
+    t0 = time.perf_counter()
+    tq_off, tq_kw = synth.lsh_training_queries(100_000, config=4)
+    tr = learned.train_predictor(idx, tq_off, tq_kw, k, epochs=20, batch=256, lr=2e-3)
+    train_s = time.perf_counter() - t0
+    Q = w.n_queries
+    d_q_off, d_q_kw = runner.to_dev(w.q_off), runner.to_dev(w.q_kw)
+    stream = torch.cuda.current_stream()
+    out_p, out_l = runner.Outputs(Q, k), runner.Outputs(Q, k)
+    seeds = torch.empty(Q, dtype=torch.int32, device="cuda")
+
+    def plain():
+        qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
+        genie.genie_search(idx, qs, k, out_p.ids, out_p.counts, out_p.n_valid, stream=stream)
+
+    def seeded(stats=None):
+        qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
+        tr["mlp"].seeds(qs, tr["margin"], seeds, stream)
+        genie.genie_search(idx, qs, k, out_l.ids, out_l.counts, out_l.n_valid,
+                           opts=genie.make_opts(d_seed=seeds, d_stats=stats), stream=stream)
+
+    for _ in range(args.warmup):
+        plain()
+        seeded()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    p_ms, _ = timed_steps(plain, args.steps, stream)
+    l_ms, per = timed_steps(seeded, args.steps, stream)
+    clk = clocks.stop()
+    st_p = torch.zeros(8, dtype=torch.int64, device="cuda")
+    st_l = torch.zeros(8, dtype=torch.int64, device="cuda")
+    qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
+    genie.genie_search(idx, qs, k, out_p.ids, out_p.counts, out_p.n_valid,
+                       opts=genie.make_opts(d_stats=st_p), stream=stream)
+    seeded(st_l)
+    a, b = out_p.host(), out_l.host()
+    identical = all(np.array_equal(a[key], b[key]) for key in a)
+    sp, sl = st_p.cpu().numpy(), st_l.cpu().numpy()
+    entries = qs.n_entries
+    line = {
+        "metric": METRIC, "value": Q * args.steps / (l_ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": l_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "impl": "genie-learned",
+        "config": {"workload": "lsh-4m learned threshold: 4,000,000 objects x 256 LSH keywords, "
+                               "4096 queries, k=100; 64-128-1 bf16 MLP trained on 100k query / "
+                               "k-th-count pairs from the plain search",
+                   "n_objects": w.n_objects, "n_queries": Q, "k": k, "entries_per_step": int(entries)},
+        "plain": {"value": Q * args.steps / (p_ms / 1e3), "ms_per_step": p_ms / args.steps,
+                  "gate_passes": int(sp[0]), "ht_inserts": int(sp[1])},
+        "learned": {"value": Q * args.steps / (l_ms / 1e3), "ms_per_step": l_ms / args.steps,
+                    "gate_passes": int(sl[0]), "ht_inserts": int(sl[1]),
+                    "reruns": int(sl[3]), "rerun_rate": float(sl[3]) / Q,
+                    "batch_p50_ms": float(np.percentile(per, 50)),
+                    "batch_p99_ms": float(np.percentile(per, 99))},
+        "speedup_vs_plain": p_ms / l_ms, "identical_results": bool(identical),
+        "training": {"seconds": train_s, "train_loss": tr["train_loss"], "margin": tr["margin"],
+                     "n_train": tr["n_train"], "n_val": tr["n_val"],
+                     "target_mean": tr["target_mean"]},
+        "entries_per_s": entries * args.steps / (l_ms / 1e3),
+        "gpu_launches": 5 * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "lsh4m-learned":
+        if rank == 0:
+            run_learned(args, rank, world, local)
     else:
         run_genie(args, rank, world, local)
     if world > 1:

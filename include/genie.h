@@ -195,9 +195,9 @@ typedef struct {
    * s = 1 (this synchronises `stream` once to read the rerun count). */
   const uint32_t* d_seed;
   /* Tuning (0 = automatic): log2 of object ids counted by one block, threads
-   * per block (512 or 1024), hash-table slots per block (power of two >= 32),
-   * 16-byte loads in flight per thread (2 or 4 with 1024 threads, 4 or 8
-   * with 512). */
+   * per block (512, 768 or 1024), hash-table slots per block (power of two
+   * >= 32), 16-byte loads in flight per thread (2 or 4 with 768 or 1024
+   * threads, 4 or 8 with 512). */
   uint32_t block_shift;
   uint32_t threads;
   uint32_t ht_slots;

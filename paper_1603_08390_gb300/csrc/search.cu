@@ -272,7 +272,6 @@ __global__ void __launch_bounds__(THREADS, 1) scan_cpq_kernel(const ScanArgs A) 
 
   uint32_t* ring = gq + warp * 2 * kRing;  // this warp's Gate queue
   uint32_t qh = 0, qn = 0;                 // head and length
-  const uint32_t lmask = (1u << A.block_shift) - 1u;
   const GateState gs{za, present, ht, bc, &s_at, s_flags};
 
   // ---- scan: all postings of the query's keywords inside this id range ---
@@ -293,18 +292,20 @@ __global__ void __launch_bounds__(THREADS, 1) scan_cpq_kernel(const ScanArgs A) 
     uint32_t total_tiles;
     uint32_t pre = dev::block_exclusive_scan(ntiles, scratch, &total_tiles);
     if (tid < nk) tile_pre[tid] = pre;
-    if (tid == 0) s_next = nwarps;
+    if (tid == 0) {
+      tile_pre[nk] = total_tiles;  // sentinel for the segment cursor
+      s_next = nwarps;
+    }
     __syncthreads();
 
-    // tiles are handed out dynamically: warps slowed by Gate work take fewer
+    // tiles are handed out dynamically (warps slowed by Gate work take
+    // fewer); a warp's tile numbers only grow, so its segment cursor j only
+    // moves forward
+    uint32_t j = 0;
     for (uint32_t t = warp; t < total_tiles;) {
-      uint32_t lo_j = 0, hi_j = nk;  // last j with tile_pre[j] <= t
-      while (hi_j - lo_j > 1) {
-        uint32_t mid = (lo_j + hi_j) >> 1;
-        if (tile_pre[mid] <= t) lo_j = mid; else hi_j = mid;
-      }
-      const uint32_t lo = seg_lo[lo_j], hi = seg_hi[lo_j];
-      const uint32_t start = (lo & ~3u) + (t - tile_pre[lo_j]) * kTile;
+      while (tile_pre[j + 1] <= t) ++j;
+      const uint32_t lo = seg_lo[j], hi = seg_hi[j];
+      const uint32_t start = (lo & ~3u) + (t - tile_pre[j]) * kTile;
       uint4 v[kUnroll];
 #pragma unroll
       for (uint32_t u = 0; u < kUnroll; ++u) {
@@ -316,11 +317,12 @@ __global__ void __launch_bounds__(THREADS, 1) scan_cpq_kernel(const ScanArgs A) 
       // lines 1-2); val = the object's new count, 0 for slots outside the list
       uint32_t val[4 * kUnroll];
       if (start >= lo && start + kTile <= hi) {  // tile inside the list: no checks
+        // the index keeps every id of this range's sublists inside the range
 #pragma unroll
         for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
           const uint32_t u = i >> 2, e = i & 3;
           const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-          const uint32_t local = (id - obj_base) & lmask;
+          const uint32_t local = id - obj_base;
           const uint32_t sh = (local & (PER - 1)) << LOG2W;
           val[i] = ((atomicAdd(&bc[local >> LPW], 1u << sh) >> sh) & MASK) + 1u;
         }
@@ -349,10 +351,10 @@ __global__ void __launch_bounds__(THREADS, 1) scan_cpq_kernel(const ScanArgs A) 
       uint32_t cm = 0;
 #pragma unroll
       for (uint32_t i = 0; i < 4 * kUnroll; ++i) cm |= (uint32_t)(val[i] >= at_c) << i;
-      const uint32_t nc = __popc(cm);
-      const uint32_t incl = dev::warp_inclusive_scan(nc);
-      const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-      if (total) {
+      if (__any_sync(0xFFFFFFFFu, cm)) {
+        const uint32_t nc = __popc(cm);
+        const uint32_t incl = dev::warp_inclusive_scan(nc);
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
         if (qn + total > kRing) {  // make room: run the Gate on the backlog
           while (qn) {
             const uint32_t f = min(qn, 32u);
@@ -614,12 +616,12 @@ genie_status make_plan(const genie_index* idx, const genie_queries* qs, uint32_t
   if (slots & (slots - 1)) return fail(GENIE_ERR_INVALID_ARG, "genie_search: ht_slots must be a power of two");
   if (slots < 32) return fail(GENIE_ERR_INVALID_ARG, "genie_search: ht_slots must be >= 32");
   p->ht_slots = slots;
-  p->threads = (o && o->threads) ? o->threads : 1024u;
-  if (p->threads != 512 && p->threads != 1024)
-    return fail(GENIE_ERR_INVALID_ARG, "genie_search: threads must be 512 or 1024");
+  p->threads = (o && o->threads) ? o->threads : 768u;
+  if (p->threads != 512 && p->threads != 768 && p->threads != 1024)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search: threads must be 512, 768 or 1024");
   p->unroll = (o && o->unroll) ? o->unroll : (p->threads == 512 ? 4u : 2u);
   if (p->threads == 512 ? (p->unroll != 4 && p->unroll != 8) : (p->unroll != 2 && p->unroll != 4))
-    return fail(GENIE_ERR_INVALID_ARG, "genie_search: unroll must be 2 or 4 (1024 threads), 4 or 8 (512)");
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search: unroll must be 2 or 4 (768 or 1024 threads), 4 or 8 (512)");
   p->za_len = B + 2;
   p->smem = scan_smem_bytes(p->log2w, shift, slots, p->za_len, k);
   int dev = 0, max_smem = 0;
@@ -644,6 +646,8 @@ template <int LOG2W>
 cudaError_t dispatch_width(const ScanArgs& a, const Plan& p, cudaStream_t s) {
   if (p.threads == 512) return p.unroll == 8 ? launch_scan<LOG2W, 8, 512>(a, p, s)
                                              : launch_scan<LOG2W, 4, 512>(a, p, s);
+  if (p.threads == 768) return p.unroll == 4 ? launch_scan<LOG2W, 4, 768>(a, p, s)
+                                             : launch_scan<LOG2W, 2, 768>(a, p, s);
   return p.unroll == 4 ? launch_scan<LOG2W, 4, 1024>(a, p, s) : launch_scan<LOG2W, 2, 1024>(a, p, s);
 }
 
