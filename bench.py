@@ -48,9 +48,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["genie", "reference"], default="genie")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["lsh1m", "lsh4m-learned"], default="lsh1m",
+    ap.add_argument("--workload", choices=["lsh1m", "lsh4m-learned", "sets4m-batched"],
+                    default="lsh1m",
                     help="lsh1m: the headline batch; lsh4m-learned: plain vs learned-seed "
-                         "search on 4M objects / 4096 queries (k=100)")
+                         "search on 4M objects / 4096 queries (k=100); sets4m-batched: plain "
+                         "launch vs the persistent graph-captured batch on 4M Zipf sets / 8192 "
+                         "queries (k=10)")
     ap.add_argument("--queries", type=int, default=N_QUERIES,
                     help="queries per batch (the workload is defined at 1024; smaller "
                          "values are for profiling captures)")
@@ -424,6 +427,95 @@ def run_learned(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, rank, world, local):
+    """Plain one-launch-per-kernel search vs the persistent, graph-captured,
+    autotuned batch on the 4M-object Zipf-set workload."""
+    import torch
+    import synth
+    from paper_1603_08390_gb300 import _build, genie, runner
+
+    _build.build()
+    torch.cuda.set_device(local)
+    k = 10
+    w = synth.config(3)
+    idx = runner.build_index(w)
+    Q = w.n_queries
+    d_q_off, d_q_kw = runner.to_dev(w.q_off), runner.to_dev(w.q_kw)
+    stream = torch.cuda.current_stream()
+    # autotune on a sample of 512 queries
+    sample = w.subset(np.arange(0, Q, Q // 512)[:512])
+    sq = runner.compile_queries(idx, sample)
+    t0 = time.perf_counter()
+    tuned = genie.genie_autotune(idx, sq, k, os.path.join(tempfile.gettempdir(), "genie_tune.txt"))
+    tune_s = time.perf_counter() - t0
+    qs0 = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
+    batch = genie.Batch(idx, Q, qs0.max_bound, k, tuned)
+    entries = qs0.n_entries
+    out_p, out_b = runner.Outputs(Q, k), runner.Outputs(Q, k)
+    topt = genie.make_opts(block_shift=tuned.block_shift, threads=tuned.threads,
+                           unroll=tuned.unroll, ht_slots=tuned.ht_slots)
+
+    def plain():
+        qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
+        genie.genie_search(idx, qs, k, out_p.ids, out_p.counts, out_p.n_valid, stream=stream)
+
+    def plain_tuned():
+        qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
+        genie.genie_search(idx, qs, k, out_p.ids, out_p.counts, out_p.n_valid, opts=topt,
+                           stream=stream)
+
+    def batched():
+        qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
+        batch.run(qs, out_b.ids, out_b.counts, out_b.n_valid, stream=stream)
+
+    for _ in range(args.warmup):
+        plain()
+        batched()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    p_ms, _ = timed_steps(plain, args.steps, stream)
+    pt_ms, _ = timed_steps(plain_tuned, args.steps, stream)
+    b_ms, per = timed_steps(batched, args.steps, stream)
+    clk = clocks.stop()
+    a, b = out_p.host(), out_b.host()
+    identical = all(np.array_equal(a[key], b[key]) for key in a)
+    rows = np.arange(0, Q, Q // 8)[:8]
+    import oracle
+    ref = oracle.topk(w.subset(rows))
+    sampled_ok = all(np.array_equal(b["ids"][q, :int(ref["n_valid"][j])],
+                                    ref["ids"][j, :int(ref["n_valid"][j])]) and
+                     b["n_valid"][q] == ref["n_valid"][j] for j, q in enumerate(rows))
+    line = {
+        "metric": METRIC, "value": Q * args.steps / (b_ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": b_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "impl": "genie-batched",
+        "config": {"workload": "sets-4m batched: 4,000,000 Zipf(1.1) keyword sets of 16-256 over "
+                               "a 2^20 vocabulary, 8192 queries of 8-512 keywords, k=10; one "
+                               "persistent CUDA-graph launch per batch, autotuned shape",
+                   "n_objects": w.n_objects, "n_queries": Q, "k": k, "entries_per_step": int(entries)},
+        "plain_default": {"value": Q * args.steps / (p_ms / 1e3), "ms_per_step": p_ms / args.steps},
+        "plain_tuned": {"value": Q * args.steps / (pt_ms / 1e3), "ms_per_step": pt_ms / args.steps},
+        "batched": {"value": Q * args.steps / (b_ms / 1e3), "ms_per_step": b_ms / args.steps,
+                    "batch_p50_ms": float(np.percentile(per, 50)),
+                    "batch_p99_ms": float(np.percentile(per, 99))},
+        "autotune": {"block_shift": tuned.block_shift, "threads": tuned.threads,
+                     "unroll": tuned.unroll, "ht_slots": tuned.ht_slots,
+                     "sample_ms": tuned.tuned_ms, "seconds": tune_s,
+                     "from_cache": bool(tuned.from_cache)},
+        "speedup_vs_plain_default": p_ms / b_ms, "identical_results": bool(identical),
+        "oracle_sampled_queries_ok": bool(sampled_ok),
+        "entries_per_s": entries * args.steps / (b_ms / 1e3),
+        "roofline": {"bound": "hbm", "achieved": 4.0 * entries / (b_ms / args.steps / 1e3) / 1e9,
+                     "peak": measured_peaks()[0], "unit": "GB/s",
+                     "frac": 4.0 * entries / (b_ms / args.steps / 1e3) / 1e9 / measured_peaks()[0],
+                     "traffic": None, "kernel": "batch_cpq_kernel (whole step)"},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup()
@@ -432,6 +524,9 @@ def main():
     elif args.workload == "lsh4m-learned":
         if rank == 0:
             run_learned(args, rank, world, local)
+    elif args.workload == "sets4m-batched":
+        if rank == 0:
+            run_batched(args, rank, world, local)
     else:
         run_genie(args, rank, world, local)
     if world > 1:

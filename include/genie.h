@@ -236,6 +236,63 @@ genie_status genie_search(const genie_index* index, const genie_queries* queries
                           uint32_t* d_counts, uint32_t* d_n_valid, genie_stream stream);
 
 /* ------------------------------------------------------------------------ */
+/* Batched search: one persistent, CUDA-graph-captured launch per batch      */
+/* ------------------------------------------------------------------------ */
+/*
+ * A batch plan runs all (query, object range) c-PQ passes of a batch in one
+ * persistent kernel (one block per SM pulling work items range by range,
+ * queries with the most postings first inside a range; Sec. 3.2.1 treats the
+ * same load-balance problem by splitting long lists) and merges each query
+ * as soon as its last range is done (the Sec. 3.4 merge, on the device).  The
+ * kernels are captured once into a CUDA graph; each batch refreshes a small
+ * descriptor and replays it.  Results equal genie_search's.
+ */
+typedef struct genie_batch genie_batch;
+
+typedef struct {
+  /* shape (0 = automatic; same meaning and limits as genie_search_opts) */
+  uint32_t block_shift;
+  uint32_t threads;
+  uint32_t unroll;
+  uint32_t ht_slots;
+  uint32_t blocks;      /* persistent blocks, 0 = one per SM */
+  float tuned_ms;       /* genie_autotune output: best time on the sample */
+  uint32_t from_cache;  /* genie_autotune output: 1 if read from the cache file */
+} genie_batch_opts;
+
+/*
+ * Autotuner: times genie_search on `sample` (compiled queries representative
+ * of the workload) for each candidate shape -- block size x 16-byte loads in
+ * flight x object-id range per block -- and writes the fastest to *out.
+ * cache_path (may be NULL): a text file of "key block_shift threads unroll
+ * ht_slots ms" lines; a line whose key (GPU, index sizes, count bound, k and
+ * the postings-per-query scale) matches is returned without timing, and a
+ * new result is appended.  Synchronises the device.
+ */
+genie_status genie_autotune(const genie_index* index, const genie_queries* sample, uint32_t k,
+                            const char* cache_path, genie_batch_opts* out);
+
+/*
+ * New batch plan for up to max_queries queries whose count bounds are at most
+ * max_bound, k results per query.  Allocates its candidate lists (max_queries
+ * x ranges x k x 8 bytes) and captures its graph.
+ */
+genie_status genie_batch_create(const genie_index* index, uint32_t max_queries, uint32_t max_bound,
+                                uint32_t k, const genie_batch_opts* opts, genie_batch** out);
+genie_status genie_batch_get_info(const genie_batch* batch, genie_batch_opts* out);
+void genie_batch_destroy(genie_batch* batch);
+
+/*
+ * Run one batch: results as genie_search (row stride = the plan's k; d_k as
+ * in genie_search, checked with one synchronisation).  Enqueued on `stream`;
+ * one plan runs one batch at a time, so issue the runs of a plan on one
+ * stream.  GENIE_ERR_CAPACITY if the batch exceeds max_queries or max_bound.
+ */
+genie_status genie_batch_run(genie_batch* batch, const genie_queries* queries, const uint32_t* d_k,
+                             uint32_t* d_ids, uint32_t* d_counts, uint32_t* d_n_valid,
+                             genie_stream stream);
+
+/* ------------------------------------------------------------------------ */
 /* k-th-count predictor: a learned AuditThreshold seed (not in the paper)    */
 /* ------------------------------------------------------------------------ */
 /*

@@ -1,0 +1,447 @@
+// Batched search in one persistent, CUDA-graph-captured launch, and the
+// autotuner that picks its tile shapes and work split.
+//
+// A batch of Q queries against an index split into G object ranges is Q x G
+// work items, each the c-PQ pass of one (query, range) (cpq_item).  One block
+// per SM pulls items from a device counter in a fixed order: range by range
+// (so that the blocks resident at one time share one range of the List Array
+// in L2), and inside a range the queries with the most postings first (a
+// longest-processing-time order, which keeps Zipf-heavy queries off the tail;
+// the paper splits long lists instead, Sec. 3.2.1).  When a block finishes the
+// last range of a query it merges that query's ranges right away (Sec. 3.4
+// merge on the device), so the whole batch is one kernel.  The order kernel
+// and the persistent kernel are captured once into a CUDA graph; each batch
+// rewrites a small descriptor in device memory and replays the graph.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "cpq_device.cuh"
+#include "device_util.cuh"
+#include "internal.h"
+
+namespace genie {
+namespace {
+
+constexpr uint32_t kOrderCap = 16384;  // queries the order kernel sorts in one block
+
+struct BatchDesc {
+  ScanArgs scan;
+  MergeArgs merge;
+  const uint64_t* entries;  // [n] postings per query
+  uint32_t* order;          // [max_queries] batch positions, heaviest first
+  uint32_t* work;           // next work item
+  uint32_t* done;           // [max_queries] finished ranges per query
+};
+
+// order[] = queries by postings scanned, descending (ties: lower position
+// first); identity for batches above kOrderCap
+__global__ void __launch_bounds__(1024) order_kernel(const BatchDesc* __restrict__ D) {
+  extern __shared__ uint4 smem_raw[];
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw);
+  const uint32_t n = D->scan.n_sel;
+  if (n > kOrderCap) {
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) D->order[i] = i;
+    return;
+  }
+  const uint32_t n2 = dev::next_pow2(max(n, 1u));
+  for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) {
+    unsigned long long k = 0;
+    if (i < n) {
+      const unsigned long long cap = (1ull << 40) - 1;
+      const unsigned long long e = D->entries[i] < cap ? (unsigned long long)D->entries[i] : cap;
+      k = (e << 24) | (unsigned long long)(0xFFFFFFu - i);
+    }
+    keys[i] = k;
+  }
+  __syncthreads();
+  dev::bitonic_sort_desc(keys, n2);
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
+    D->order[i] = 0xFFFFFFu - (uint32_t)(keys[i] & 0xFFFFFFull);
+}
+
+template <int LOG2W, int U, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) batch_cpq_kernel(const BatchDesc* __restrict__ D) {
+  extern __shared__ uint4 smem_raw[];
+  __shared__ BlockShared S;
+  __shared__ MergeShared MS;
+  __shared__ ScanArgs SA;
+  __shared__ MergeArgs SM;
+  __shared__ uint32_t s_last;
+  if (threadIdx.x == 0) {
+    SA = D->scan;
+    SM = D->merge;
+  }
+  __syncthreads();
+  const uint32_t Q = SA.n_sel, G = SA.n_groups;
+  const uint32_t total = Q * G;
+  unsigned long long* buf = reinterpret_cast<unsigned long long*>(smem_raw);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(buf + dev::next_pow2(SA.k));
+  for (;;) {
+    if (threadIdx.x == 0) S.item = atomicAdd(D->work, 1u);
+    __syncthreads();
+    const uint32_t item = S.item;
+    if (item >= total) break;
+    const uint32_t g = item / Q;
+    const uint32_t qi = D->order[item - g * Q];
+    cpq_item<LOG2W, U>(SA, qi, g, smem_raw, S);
+    __threadfence();  // this item's candidate list, visible to the merging block
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&D->done[qi], 1u) == G - 1;
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      merge_query<true>(SM, qi, buf, hist, MS);
+    }
+    __syncthreads();
+  }
+}
+
+// launch = false only raises the kernel's shared-memory limit (done before a
+// stream capture begins)
+template <int LOG2W, int U, int THREADS>
+cudaError_t launch_batch(const BatchDesc* d, uint32_t blocks, size_t smem, cudaStream_t s,
+                         bool launch) {
+  auto kern = batch_cpq_kernel<LOG2W, U, THREADS>;
+  if (!launch) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kern<<<blocks, THREADS, smem, s>>>(d);
+  return cudaGetLastError();
+}
+
+template <int LOG2W>
+cudaError_t batch_width(const BatchDesc* d, uint32_t blocks, size_t smem, uint32_t threads,
+                        uint32_t unroll, cudaStream_t s, bool launch) {
+  if (threads == 512) return unroll == 8 ? launch_batch<LOG2W, 8, 512>(d, blocks, smem, s, launch)
+                                         : launch_batch<LOG2W, 4, 512>(d, blocks, smem, s, launch);
+  if (threads == 768) return unroll == 4 ? launch_batch<LOG2W, 4, 768>(d, blocks, smem, s, launch)
+                                         : launch_batch<LOG2W, 2, 768>(d, blocks, smem, s, launch);
+  return unroll == 4 ? launch_batch<LOG2W, 4, 1024>(d, blocks, smem, s, launch)
+                     : launch_batch<LOG2W, 2, 1024>(d, blocks, smem, s, launch);
+}
+
+cudaError_t batch_dispatch(const genie_batch* b, bool launch);
+
+std::string tune_key(const genie_index* idx, const genie_queries* qs, uint32_t k) {
+  cudaDeviceProp prop;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaGetDeviceProperties(&prop, dev);
+  // postings per query, bucketed by powers of two, describes the workload
+  const double epq = qs->n_queries ? (double)qs->n_entries / qs->n_queries : 0.0;
+  std::ostringstream os;
+  os << prop.name << "|sm" << prop.multiProcessorCount << "|N" << idx->n_objects << "|V"
+     << idx->vocab << "|nnz" << idx->nnz << "|cs" << idx->chunk_shift << "|B" << qs->max_bound
+     << "|k" << k << "|epq2^" << (int)std::floor(std::log2(std::max(1.0, epq)));
+  std::string key = os.str();
+  std::replace(key.begin(), key.end(), ' ', '_');
+  return key;
+}
+
+}  // namespace
+}  // namespace genie
+
+struct genie_batch {
+  const genie_index* index = nullptr;
+  int device = 0;
+  uint32_t max_queries = 0, max_bound = 0, k = 0;
+  uint32_t log2w = 0, block_shift = 0, n_groups = 0, threads = 0, unroll = 0, ht_slots = 0;
+  uint32_t blocks = 0;
+  size_t smem = 0;
+  genie::BatchDesc host_desc{};
+  genie::BatchDesc* desc = nullptr;
+  unsigned long long* cand = nullptr;
+  uint32_t* order = nullptr;
+  uint32_t* counters = nullptr;  // [0] work, [1 ..] done
+  cudaStream_t capture_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+using namespace genie;
+
+namespace genie {
+namespace {
+cudaError_t batch_dispatch(const genie_batch* b, bool launch) {
+  cudaStream_t s = b->capture_stream;
+  return b->log2w == 2 ? batch_width<2>(b->desc, b->blocks, b->smem, b->threads, b->unroll, s, launch)
+       : b->log2w == 3 ? batch_width<3>(b->desc, b->blocks, b->smem, b->threads, b->unroll, s, launch)
+                       : batch_width<4>(b->desc, b->blocks, b->smem, b->threads, b->unroll, s, launch);
+}
+}  // namespace
+}  // namespace genie
+
+namespace {
+void free_batch(genie_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  cudaFree(b->desc);
+  cudaFree(b->cand);
+  cudaFree(b->order);
+  cudaFree(b->counters);
+  delete b;
+}
+}  // namespace
+
+extern "C" genie_status genie_batch_create(const genie_index* index, uint32_t max_queries,
+                                           uint32_t max_bound, uint32_t k,
+                                           const genie_batch_opts* opts, genie_batch** out) {
+  if (!index || !out) return fail(GENIE_ERR_INVALID_ARG, "genie_batch_create: NULL argument");
+  if (max_queries == 0 || max_queries > (1u << 24))
+    return fail(GENIE_ERR_INVALID_ARG, "genie_batch_create: max_queries must be in 1..2^24");
+  if (max_bound == 0 || max_bound > GENIE_MAX_BOUND)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_batch_create: max_bound must be in 1..GENIE_MAX_BOUND");
+  if (k == 0 || k > GENIE_MAX_K) return fail(GENIE_ERR_INVALID_ARG, "genie_batch_create: k must be in 1..GENIE_MAX_K");
+  genie_queries probe;  // only the fields make_plan reads
+  probe.index = index;
+  probe.max_bound = max_bound;
+  genie_search_opts so;
+  std::memset(&so, 0, sizeof(so));
+  if (opts) {
+    so.block_shift = opts->block_shift;
+    so.threads = opts->threads;
+    so.unroll = opts->unroll;
+    so.ht_slots = opts->ht_slots;
+  }
+  Plan p;
+  genie_status st = make_plan(index, &probe, k, &so, &p);
+  if (st != GENIE_OK) return st;
+  genie_batch* b = new (std::nothrow) genie_batch();
+  if (!b) return fail(GENIE_ERR_OUT_OF_MEMORY, "genie_batch_create: host allocation");
+  cudaGetDevice(&b->device);
+  b->index = index;
+  b->max_queries = max_queries;
+  b->max_bound = max_bound;
+  b->k = k;
+  b->log2w = p.log2w;
+  b->block_shift = p.block_shift;
+  b->n_groups = p.n_groups;
+  b->threads = p.threads;
+  b->unroll = p.unroll;
+  b->ht_slots = p.ht_slots;
+  b->smem = p.smem;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  b->blocks = (opts && opts->blocks) ? opts->blocks : (uint32_t)sms;
+  const size_t merge_smem = (size_t)dev::next_pow2(k) * 8 + (size_t)p.za_len * 4;
+  b->smem = std::max(b->smem, merge_smem);
+  cudaError_t e = cudaMalloc(&b->desc, sizeof(BatchDesc));
+  if (e == cudaSuccess) e = cudaMalloc(&b->cand, (uint64_t)max_queries * p.n_groups * k * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&b->order, (uint64_t)max_queries * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&b->counters, ((uint64_t)max_queries + 1) * 4);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    free_batch(b);
+    return fail_cuda(e, "genie_batch_create");
+  }
+  // fixed part of the descriptor; per-batch fields are filled by genie_batch_run
+  BatchDesc& d = b->host_desc;
+  std::memset(&d, 0, sizeof(d));
+  d.scan.kw_off = index->kw_off;
+  d.scan.post_ids = index->post_ids;
+  d.scan.chunk_pos = index->chunk_pos;
+  d.scan.n_chunks = index->n_chunks;
+  d.scan.chunk_shift = index->chunk_shift;
+  d.scan.n_objects = index->n_objects;
+  d.scan.k = k;
+  d.scan.block_shift = p.block_shift;
+  d.scan.chunks_per_block = 1u << (p.block_shift - index->chunk_shift);
+  d.scan.n_groups = p.n_groups;
+  d.scan.ht_slots = p.ht_slots;
+  d.scan.za_len = p.za_len;
+  d.scan.cand = b->cand;
+  d.merge.cand = b->cand;
+  d.merge.n_groups = p.n_groups;
+  d.merge.k = k;
+  d.merge.za_len = p.za_len;
+  d.order = b->order;
+  d.work = b->counters;
+  d.done = b->counters + 1;
+  // capture: clear counters, order the queries, run the persistent kernel
+  cudaStream_t cs = b->capture_stream;
+  const size_t osmem = (size_t)dev::next_pow2(std::min(max_queries, kOrderCap)) * 8;
+  e = cudaFuncSetAttribute(order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem);
+  if (e == cudaSuccess) e = batch_dispatch(b, false);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaMemsetAsync(b->counters, 0, ((uint64_t)max_queries + 1) * 4, cs);
+    order_kernel<<<1, 1024, osmem, cs>>>(b->desc);
+    cudaError_t le = batch_dispatch(b, true);
+    e = cudaStreamEndCapture(cs, &b->graph);
+    if (e == cudaSuccess && le != cudaSuccess) e = le;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) {
+    free_batch(b);
+    return fail_cuda(e, "genie_batch_create: graph capture");
+  }
+  *out = b;
+  return GENIE_OK;
+}
+
+extern "C" void genie_batch_destroy(genie_batch* batch) {
+  if (!batch) return;
+  cudaDeviceSynchronize();
+  free_batch(batch);
+}
+
+extern "C" genie_status genie_batch_get_info(const genie_batch* b, genie_batch_opts* out) {
+  if (!b || !out) return fail(GENIE_ERR_INVALID_ARG, "genie_batch_get_info: NULL argument");
+  out->block_shift = b->block_shift;
+  out->threads = b->threads;
+  out->unroll = b->unroll;
+  out->ht_slots = b->ht_slots;
+  out->blocks = b->blocks;
+  return GENIE_OK;
+}
+
+extern "C" genie_status genie_batch_run(genie_batch* b, const genie_queries* queries,
+                                        const uint32_t* d_k, uint32_t* d_ids, uint32_t* d_counts,
+                                        uint32_t* d_n_valid, genie_stream stream) {
+  if (!b || !queries || !d_ids || !d_counts || !d_n_valid)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_batch_run: NULL argument");
+  if (queries->index != b->index)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_batch_run: queries were compiled for another index");
+  if (queries->n_queries > b->max_queries)
+    return fail(GENIE_ERR_CAPACITY, "genie_batch_run: more queries than the batch was created for");
+  if (queries->max_bound > b->max_bound)
+    return fail(GENIE_ERR_CAPACITY, "genie_batch_run: a query's count bound exceeds the batch's max_bound");
+  cudaStream_t s = as_stream(stream);
+  if (d_k) {  // per-query k must lie in 1..k (one synchronisation)
+    uint32_t bad = 0;
+    GENIE_CUDA_TRY(cudaMemsetAsync(b->counters, 0, 4, s));
+    check_k_kernel<<<std::min<uint32_t>((queries->n_queries + 255) / 256, 1024u), 256, 0, s>>>(
+        queries->n_queries, b->k, d_k, b->counters);
+    GENIE_CUDA_TRY(cudaMemcpyAsync(&bad, b->counters, 4, cudaMemcpyDeviceToHost, s));
+    GENIE_CUDA_TRY(cudaStreamSynchronize(s));
+    if (bad) return fail(GENIE_ERR_INVALID_ARG, "genie_batch_run: a per-query k is 0 or larger than k");
+  }
+  BatchDesc d = b->host_desc;
+  d.scan.q_off = queries->q_off;
+  d.scan.q_kw = queries->q_kw;
+  d.scan.bound = queries->bound;
+  d.scan.q_sel = nullptr;
+  d.scan.n_sel = queries->n_queries;
+  d.scan.k_arr = d_k;
+  d.scan.seed = nullptr;
+  d.scan.chunk_at = nullptr;
+  d.scan.stats = nullptr;
+  d.merge.n_sel = queries->n_queries;
+  d.merge.q_sel = nullptr;
+  d.merge.k_arr = d_k;
+  d.merge.bound = queries->bound;
+  d.merge.ids = d_ids;
+  d.merge.counts = d_counts;
+  d.merge.n_valid = d_n_valid;
+  d.entries = queries->entries;
+  // pageable source: the runtime stages it before returning, so `d` may go
+  GENIE_CUDA_TRY(cudaMemcpyAsync(b->desc, &d, sizeof(d), cudaMemcpyHostToDevice, s));
+  GENIE_CUDA_TRY(cudaGraphLaunch(b->exec, s));
+  return GENIE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner
+// ---------------------------------------------------------------------------
+
+extern "C" genie_status genie_autotune(const genie_index* index, const genie_queries* sample,
+                                       uint32_t k, const char* cache_path, genie_batch_opts* out) {
+  if (!index || !sample || !out) return fail(GENIE_ERR_INVALID_ARG, "genie_autotune: NULL argument");
+  if (k == 0 || k > GENIE_MAX_K) return fail(GENIE_ERR_INVALID_ARG, "genie_autotune: k must be in 1..GENIE_MAX_K");
+  const std::string key = tune_key(index, sample, k);
+  if (cache_path && *cache_path) {
+    std::ifstream in(cache_path);
+    std::string line;
+    while (std::getline(in, line)) {
+      std::istringstream ls(line);
+      std::string kk;
+      genie_batch_opts o;
+      std::memset(&o, 0, sizeof(o));
+      if ((ls >> kk >> o.block_shift >> o.threads >> o.unroll >> o.ht_slots >> o.tuned_ms) && kk == key) {
+        *out = o;
+        out->from_cache = 1;
+        return GENIE_OK;
+      }
+    }
+  }
+  // candidate shapes: block size x loads in flight x object range per block
+  genie_queries probe;
+  probe.index = index;
+  probe.max_bound = sample->max_bound;
+  Plan base;
+  genie_status st = make_plan(index, &probe, k, nullptr, &base);
+  if (st != GENIE_OK) return st;
+  std::vector<genie_batch_opts> cands;
+  const uint32_t shapes[][2] = {{768, 2}, {768, 4}, {1024, 2}, {1024, 4}, {512, 4}};
+  for (uint32_t ds = 0; ds < 2; ++ds) {
+    uint32_t bs = base.block_shift - ds;
+    if (ds && bs < index->chunk_shift) continue;
+    for (auto& sh : shapes) {
+      genie_batch_opts o;
+      std::memset(&o, 0, sizeof(o));
+      o.block_shift = bs;
+      o.threads = sh[0];
+      o.unroll = sh[1];
+      o.ht_slots = base.ht_slots;
+      cands.push_back(o);
+    }
+  }
+  const uint32_t Q = sample->n_queries;
+  uint32_t *ids = nullptr, *cnt = nullptr, *nv = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&ids, (uint64_t)Q * k * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&cnt, (uint64_t)Q * k * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&nv, (uint64_t)Q * 4);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 1e30f;
+  genie_batch_opts best_o = cands.empty() ? genie_batch_opts{} : cands[0];
+  for (size_t c = 0; c < cands.size() && e == cudaSuccess; ++c) {
+    genie_search_opts so;
+    std::memset(&so, 0, sizeof(so));
+    so.block_shift = cands[c].block_shift;
+    so.threads = cands[c].threads;
+    so.unroll = cands[c].unroll;
+    so.ht_slots = cands[c].ht_slots;
+    float t = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {  // first run warms up
+      cudaEventRecord(e0, s);
+      st = genie_search(index, sample, k, nullptr, &so, ids, cnt, nv, (genie_stream)s);
+      cudaEventRecord(e1, s);
+      if (st != GENIE_OK) break;
+      e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) t = std::min(t, ms);
+    }
+    if (st != GENIE_OK) { st = GENIE_OK; continue; }  // a shape this GPU cannot run
+    cands[c].tuned_ms = t;
+    if (t < best) {
+      best = t;
+      best_o = cands[c];
+    }
+  }
+  cudaFree(ids);
+  cudaFree(cnt);
+  cudaFree(nv);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  if (e != cudaSuccess) return fail_cuda(e, "genie_autotune");
+  *out = best_o;
+  out->from_cache = 0;
+  if (cache_path && *cache_path) {
+    std::ofstream o(cache_path, std::ios::app);
+    o << key << " " << best_o.block_shift << " " << best_o.threads << " " << best_o.unroll << " "
+      << best_o.ht_slots << " " << best_o.tuned_ms << "\n";
+  }
+  return GENIE_OK;
+}

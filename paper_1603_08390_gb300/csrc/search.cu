@@ -44,529 +44,12 @@
 #include <mutex>
 #include <string>
 
+#include "cpq_device.cuh"
 #include "device_util.cuh"
 #include "internal.h"
 
 namespace genie {
 namespace {
-
-constexpr uint32_t kKwBatch = 512;  // query keywords staged in shared memory per round
-
-struct ScanArgs {
-  const uint64_t* kw_off;
-  const uint32_t* post_ids;
-  const uint32_t* chunk_pos;
-  uint32_t n_chunks;
-  uint32_t chunk_shift;
-  uint32_t n_objects;
-  const uint32_t* q_off;
-  const uint32_t* q_kw;
-  const uint32_t* bound;
-  const uint32_t* q_sel;  // NULL: block query index = query id
-  uint32_t n_sel;
-  uint32_t k;             // row stride of the candidate lists
-  const uint32_t* k_arr;  // per-query k or NULL
-  const uint32_t* seed;   // per-query AuditThreshold seed or NULL
-  uint32_t block_shift;
-  uint32_t chunks_per_block;
-  uint32_t n_groups;
-  uint32_t ht_slots;
-  uint32_t za_len;
-  unsigned long long* cand;  // [n_sel][n_groups][k]
-  uint32_t* chunk_at;        // [n_sel][n_groups] or NULL
-  unsigned long long* stats;
-};
-
-constexpr uint32_t kMaxProbe = 32;   // hash-table probes before an insert gives up
-constexpr uint32_t kEmpty = 0xFFFFFFFFu;
-constexpr uint32_t kMaxWarps = 32;   // per-warp Gate queues
-constexpr uint32_t kRing = 64;       // Gate candidates a warp can hold (power of two)
-
-size_t scan_smem_bytes(uint32_t log2w, uint32_t block_shift, uint32_t ht_slots, uint32_t za_len,
-                       uint32_t k) {
-  size_t words = ((size_t)1 << block_shift) >> (5 - log2w);
-  size_t present = ((size_t)1 << block_shift) >> 5;
-  return words * 4 + present * 4 + (size_t)ht_slots * 4 + (size_t)dev::next_pow2(k) * 8 +
-         (size_t)za_len * 4 + (3 * kKwBatch + 4) * 4 + (size_t)kMaxWarps * kRing * 2 * 4;
-}
-
-__device__ __forceinline__ uint32_t vld(const uint32_t* p) { return *(const volatile uint32_t*)p; }
-
-// First `limit` lanes (ascending id) whose count equals `value` (or is at
-// least `value` when AT_LEAST) become result keys dst[0..); returns how many.
-template <int LOG2W, bool AT_LEAST>
-__device__ uint32_t collect_lanes(const uint32_t* bc, uint32_t nwords, uint32_t value,
-                                  uint32_t limit, uint32_t obj_base, unsigned long long* dst,
-                                  uint32_t* scratch) {
-  constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, MASK = (1u << W) - 1u;
-  const uint32_t per = (nwords + blockDim.x - 1) / blockDim.x;
-  const uint32_t wa = min(nwords, threadIdx.x * per), wb = min(nwords, wa + per);
-  uint32_t m = 0;
-  for (uint32_t w = wa; w < wb; ++w) {
-    uint32_t word = bc[w];
-#pragma unroll
-    for (uint32_t l = 0; l < PER; ++l) {
-      uint32_t v = (word >> (l * W)) & MASK;
-      m += AT_LEAST ? (v >= value) : (v == value);
-    }
-  }
-  uint32_t total;
-  uint32_t pos = dev::block_exclusive_scan(m, scratch, &total);
-  if (pos < limit) {
-    for (uint32_t w = wa; w < wb && pos < limit; ++w) {
-      uint32_t word = bc[w];
-#pragma unroll
-      for (uint32_t l = 0; l < PER; ++l) {
-        uint32_t v = (word >> (l * W)) & MASK;
-        if ((AT_LEAST ? (v >= value) : (v == value)) && pos < limit)
-          dst[pos++] = dev::result_key(v, obj_base + w * PER + l);
-      }
-    }
-  }
-  return min(total, limit);
-}
-
-template <int LOG2W>
-__device__ __forceinline__ uint32_t lane_count(const uint32_t* bc, uint32_t local) {
-  constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, LPW = 5 - LOG2W, MASK = (1u << W) - 1u;
-  return (vld(&bc[local >> LPW]) >> ((local & (PER - 1)) << LOG2W)) & MASK;
-}
-
-// State the Gate touches, all in shared memory of one block.
-struct GateState {
-  uint32_t* za;       // ZipperArray, 1-based
-  uint32_t* present;  // one bit per object of the range: has a hash-table entry
-  uint32_t* ht;       // hash table of candidate ids
-  const uint32_t* bc; // Bitmap Counter
-  uint32_t* at;       // AuditThreshold
-  uint32_t* flags;    // [0] an insert found no slot, [1] a count above the bound
-};
-
-// Hash-table insert of a candidate id (once per object while it is flagged
-// present).  A slot is free when empty or when its object's exact count has
-// fallen below AT - 1 (Sec. 3.3.2); the evicted object loses its flag.
-template <int LOG2W>
-__device__ __noinline__ void ht_insert(const GateState g, uint32_t id, uint32_t obj_base,
-                                       uint32_t ht_mask, uint32_t ht_bits) {
-  uint32_t slot = ht_bits ? (id * 2654435761u) >> (32 - ht_bits) : 0u;
-  for (uint32_t probe = 0; probe < kMaxProbe; ++probe, slot = (slot + 1) & ht_mask) {
-    uint32_t e = vld(&g.ht[slot]);
-    for (;;) {
-      bool free_slot = e == kEmpty;
-      if (!free_slot) free_slot = lane_count<LOG2W>(g.bc, e - obj_base) + 1 < vld(g.at);
-      if (!free_slot) break;
-      uint32_t prev = atomicCAS(&g.ht[slot], e, id);
-      if (prev == e) {
-        if (e != kEmpty) {
-          uint32_t le = e - obj_base;
-          atomicAnd(&g.present[le >> 5], ~(1u << (le & 31)));
-        }
-        return;
-      }
-      e = prev;
-    }
-  }
-  g.flags[0] = 1;  // not placed: the read-out falls back to the Bitmap Counter
-}
-
-// The Gate of Algorithm 1 for n <= 32 candidates queued by one warp (lane l
-// takes entry head + l of the warp's ring).  Passes at the same level share one ZipperArray atomic;
-// z numbers a pass within its level; the first k passes of a level are
-// hash-table candidates; a full level advances AT.  Returns the passes of
-// this lane (0/1) and adds its inserts to *n_ins.
-template <int LOG2W>
-__device__ __noinline__ uint32_t gate_flush(const GateState g, const uint32_t* ring, uint32_t head,
-                                            uint32_t n, uint32_t kq, uint32_t B, uint32_t obj_base,
-                                            uint32_t ht_mask, uint32_t ht_bits, uint32_t* n_ins) {
-  const uint32_t lane = dev::lane_id();
-  __syncwarp();
-  const bool act = lane < n;
-  const uint32_t slot = (head + lane) & (kRing - 1);
-  const uint32_t id = act ? ring[slot] : 0u;
-  const uint32_t val = act ? ring[kRing + slot] : 0u;
-  __syncwarp();
-  if (act && val > B) g.flags[1] = 1;  // cannot happen with a valid bound
-  const bool pass = act && val >= vld(g.at) && val <= B;
-  const uint32_t m = __ballot_sync(0xFFFFFFFFu, pass);
-  if (!pass) return 0;
-  const uint32_t peers = __match_any_sync(m, val);
-  const uint32_t leader = __ffs(peers) - 1, n_peers = __popc(peers);
-  const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(&g.za[val], n_peers);
-  base = __shfl_sync(peers, base, leader);
-  const uint32_t z = base + rank;
-  if (z < kq) {
-    const uint32_t local = id - obj_base;
-    const uint32_t w = local >> 5, b = 1u << (local & 31);
-    if (!(vld(&g.present[w]) & b) && !(atomicOr(&g.present[w], b) & b)) {
-      ++*n_ins;
-      ht_insert<LOG2W>(g, id, obj_base, ht_mask, ht_bits);
-    }
-  }
-  if (rank == n_peers - 1 && z + 1 >= kq) {  // level full: advance AT
-    uint32_t a = vld(g.at);
-    while (a <= B && vld(&g.za[a]) >= kq) {
-      atomicMax(g.at, a + 1);
-      ++a;
-    }
-  }
-  return 1;
-}
-
-// LOG2W: log2 of the counter width; U: 16-byte loads in flight per lane (a
-// warp tile is 128 * U postings); THREADS: block size.
-template <int LOG2W, int U, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1) scan_cpq_kernel(const ScanArgs A) {
-  constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, LPW = 5 - LOG2W, MASK = (1u << W) - 1u;
-  constexpr uint32_t kUnroll = U, kTile = 32 * 4 * U;
-  extern __shared__ uint4 smem_raw[];
-  __shared__ uint32_t s_at, s_n, s_next;
-  __shared__ uint32_t s_flags[2];  // [0] hash table incomplete, [1] inconsistent input
-  __shared__ uint32_t scratch[33];
-  __shared__ unsigned long long scratch64[33];
-
-  // shared-memory layout: Bitmap Counter | presence bits | Hash Table | read-out
-  // buffer | ZipperArray | staged keyword segments
-  const uint32_t nwords = (1u << A.block_shift) >> LPW;
-  const uint32_t npresent = (1u << A.block_shift) >> 5;
-  const uint32_t kpad = dev::next_pow2(A.k);
-  uint32_t* bc = reinterpret_cast<uint32_t*>(smem_raw);
-  uint32_t* present = bc + nwords;
-  uint32_t* ht = present + npresent;
-  unsigned long long* cand = reinterpret_cast<unsigned long long*>(ht + A.ht_slots);
-  uint32_t* za = reinterpret_cast<uint32_t*>(cand + kpad);
-  uint32_t* seg_lo = za + A.za_len;
-  uint32_t* seg_hi = seg_lo + kKwBatch;
-  uint32_t* tile_pre = seg_hi + kKwBatch;
-  uint32_t* gq = tile_pre + kKwBatch + 4;  // [warp][id x kRing | val x kRing]
-
-  const uint32_t tid = threadIdx.x, lane = dev::lane_id(), warp = dev::warp_id();
-  const uint32_t nwarps = blockDim.x >> 5;
-  const uint32_t qi = blockIdx.x % A.n_sel, g = blockIdx.x / A.n_sel;
-  const uint32_t q = A.q_sel ? A.q_sel[qi] : qi;
-  const uint32_t kq = A.k_arr ? A.k_arr[q] : A.k;
-  const uint32_t B = A.bound[q];
-  const uint32_t obj_base = g << A.block_shift;
-  const uint32_t n_local = min(1u << A.block_shift, A.n_objects - obj_base);
-  const uint32_t c0 = g * A.chunks_per_block, c1 = min(c0 + A.chunks_per_block, A.n_chunks);
-  const uint32_t ht_mask = A.ht_slots - 1, ht_bits = 31 - __clz(A.ht_slots);
-
-  // ---- reset this block's c-PQ ------------------------------------------
-  {
-    uint4* b4 = reinterpret_cast<uint4*>(bc);
-    const uint4 z4 = make_uint4(0, 0, 0, 0);
-    for (uint32_t i = tid; i < ((nwords + npresent) >> 2); i += blockDim.x) b4[i] = z4;
-    for (uint32_t i = tid; i < A.ht_slots; i += blockDim.x) ht[i] = kEmpty;
-    for (uint32_t i = tid; i < B + 2; i += blockDim.x) za[i] = 0;
-    if (tid == 0) {
-      uint32_t s0 = A.seed ? A.seed[q] : 1u;
-      s_at = max(1u, min(s0, B + 1));
-      s_flags[0] = 0;
-      s_flags[1] = 0;
-    }
-  }
-  __syncthreads();
-
-  uint32_t n_gate = 0, n_ins = 0;
-
-  uint32_t* ring = gq + warp * 2 * kRing;  // this warp's Gate queue
-  uint32_t qh = 0, qn = 0;                 // head and length
-  const GateState gs{za, present, ht, bc, &s_at, s_flags};
-
-  // ---- scan: all postings of the query's keywords inside this id range ---
-  const uint32_t qa = A.q_off[q], qb = A.q_off[q + 1];
-  const uint32_t stride = A.n_chunks + 1;
-  for (uint32_t kb = qa; kb < qb; kb += kKwBatch) {
-    const uint32_t nk = min(kKwBatch, qb - kb);
-    uint32_t ntiles = 0;
-    if (tid < nk) {
-      const uint32_t kw = A.q_kw[kb + tid];
-      const uint64_t base = A.kw_off[kw];
-      const uint32_t* row = A.chunk_pos + (uint64_t)kw * stride;
-      const uint32_t lo = (uint32_t)(base + row[c0]), hi = (uint32_t)(base + row[c1]);
-      seg_lo[tid] = lo;
-      seg_hi[tid] = hi;
-      ntiles = hi > lo ? (hi - (lo & ~3u) + kTile - 1) / kTile : 0;
-    }
-    uint32_t total_tiles;
-    uint32_t pre = dev::block_exclusive_scan(ntiles, scratch, &total_tiles);
-    if (tid < nk) tile_pre[tid] = pre;
-    if (tid == 0) {
-      tile_pre[nk] = total_tiles;  // sentinel for the segment cursor
-      s_next = nwarps;
-    }
-    __syncthreads();
-
-    // tiles are handed out dynamically (warps slowed by Gate work take
-    // fewer); a warp's tile numbers only grow, so its segment cursor j only
-    // moves forward
-    uint32_t j = 0;
-    for (uint32_t t = warp; t < total_tiles;) {
-      while (tile_pre[j + 1] <= t) ++j;
-      const uint32_t lo = seg_lo[j], hi = seg_hi[j];
-      const uint32_t start = (lo & ~3u) + (t - tile_pre[j]) * kTile;
-      uint4 v[kUnroll];
-#pragma unroll
-      for (uint32_t u = 0; u < kUnroll; ++u) {
-        const uint32_t idx = start + (u * 32 + lane) * 4;
-        v[u] = idx < hi ? __ldg(reinterpret_cast<const uint4*>(A.post_ids + idx))
-                        : make_uint4(0, 0, 0, 0);
-      }
-      // Bitmap Counter: one sub-word atomic add per posting (Algorithm 1,
-      // lines 1-2); val = the object's new count, 0 for slots outside the list
-      uint32_t val[4 * kUnroll];
-      if (start >= lo && start + kTile <= hi) {  // tile inside the list: no checks
-        // the index keeps every id of this range's sublists inside the range
-#pragma unroll
-        for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
-          const uint32_t u = i >> 2, e = i & 3;
-          const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-          const uint32_t local = id - obj_base;
-          const uint32_t sh = (local & (PER - 1)) << LOG2W;
-          val[i] = ((atomicAdd(&bc[local >> LPW], 1u << sh) >> sh) & MASK) + 1u;
-        }
-      } else {
-#pragma unroll
-        for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
-          const uint32_t u = i >> 2, e = i & 3;
-          const uint32_t pos = start + (u * 32 + lane) * 4 + e;
-          const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-          const uint32_t local = id - obj_base;
-          val[i] = 0;
-          if (pos >= lo && pos < hi) {
-            if (local < n_local) {
-              const uint32_t sh = (local & (PER - 1)) << LOG2W;
-              val[i] = ((atomicAdd(&bc[local >> LPW], 1u << sh) >> sh) & MASK) + 1u;
-            } else {
-              s_flags[1] = 1;  // an id outside this block's range: the index is inconsistent
-            }
-          }
-        }
-      }
-      // Gate (Algorithm 1, lines 3-7): postings whose new count reaches the
-      // (possibly stale) AuditThreshold join the warp's queue; the warp runs
-      // the Gate on 32 queued candidates at a time.
-      const uint32_t at_c = vld(&s_at);
-      uint32_t cm = 0;
-#pragma unroll
-      for (uint32_t i = 0; i < 4 * kUnroll; ++i) cm |= (uint32_t)(val[i] >= at_c) << i;
-      if (__any_sync(0xFFFFFFFFu, cm)) {
-        const uint32_t nc = __popc(cm);
-        const uint32_t incl = dev::warp_inclusive_scan(nc);
-        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        if (qn + total > kRing) {  // make room: run the Gate on the backlog
-          while (qn) {
-            const uint32_t f = min(qn, 32u);
-            n_gate += gate_flush<LOG2W>(gs, ring, qh, f, kq, B, obj_base, ht_mask, ht_bits, &n_ins);
-            qh += f;
-            qn -= f;
-          }
-        }
-        if (total <= kRing) {
-          uint32_t p = qh + qn + incl - nc;
-#pragma unroll
-          for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
-            if ((cm >> i) & 1u) {
-              const uint32_t u = i >> 2, e = i & 3;
-              ring[p & (kRing - 1)] = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-              ring[kRing + (p & (kRing - 1))] = val[i];
-              ++p;
-            }
-          }
-          qn += total;
-          while (qn >= 32) {
-            n_gate += gate_flush<LOG2W>(gs, ring, qh, 32, kq, B, obj_base, ht_mask, ht_bits, &n_ins);
-            qh += 32;
-            qn -= 32;
-          }
-        } else {  // a burst larger than the queue: one element slot at a time
-#pragma unroll
-          for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
-            const bool c = (cm >> i) & 1u;
-            const uint32_t m = __ballot_sync(0xFFFFFFFFu, c);
-            if (m == 0) continue;
-            if (c) {
-              const uint32_t u = i >> 2, e = i & 3;
-              const uint32_t p = (qh + __popc(m & ((1u << lane) - 1u))) & (kRing - 1);
-              ring[p] = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-              ring[kRing + p] = val[i];
-            }
-            n_gate += gate_flush<LOG2W>(gs, ring, qh, __popc(m), kq, B, obj_base, ht_mask, ht_bits,
-                                        &n_ins);
-          }
-        }
-      }
-      uint32_t nt = 0;
-      if (lane == 0) nt = atomicAdd(&s_next, 1u);
-      t = __shfl_sync(0xFFFFFFFFu, nt, 0);
-    }
-    while (qn) {
-      const uint32_t f = min(qn, 32u);
-      n_gate += gate_flush<LOG2W>(gs, ring, qh, f, kq, B, obj_base, ht_mask, ht_bits, &n_ins);
-      qh += f;
-      qn -= f;
-    }
-    __syncthreads();
-  }
-
-  // ---- finalise AT (Lemma 3.1) and read out this range's top-k ----------
-  if (tid == 0) {
-    uint32_t a = s_at;
-    while (a <= B && za[a] >= kq) ++a;
-    s_at = a;
-    s_n = 0;
-  }
-  __syncthreads();
-  const uint32_t at_f = s_at;
-  const uint32_t nwords_local = (n_local + PER - 1) / PER;
-  unsigned long long* out = A.cand + ((unsigned long long)qi * A.n_groups + g) * A.k;
-  // Theorem 3.1: the objects with count >= AT_f are candidates in the HT; their
-  // number is exactly ZA[AT_f] (every object at or above AT_f passed that level
-  // through the Gate), which certifies the read-out.
-  const uint32_t want = za[at_f];
-  for (uint32_t i = tid; i < A.ht_slots; i += blockDim.x) {
-    uint32_t id = ht[i];
-    if (id == kEmpty) continue;
-    uint32_t c = lane_count<LOG2W>(bc, id - obj_base);
-    if (c >= at_f) {
-      uint32_t p = atomicAdd(&s_n, 1u);
-      if (p < kpad) cand[p] = dev::result_key(c, id);
-    }
-  }
-  __syncthreads();
-  uint32_t n_hi = s_n;
-  const bool certified = !s_flags[0] && n_hi == want && n_hi < kq;
-  if (!certified)  // Bitmap-Counter selection of the same set
-    n_hi = collect_lanes<LOG2W, true>(bc, nwords_local, at_f, kq, obj_base, cand, scratch);
-  __syncthreads();
-  {
-    const uint32_t n2 = dev::next_pow2(max(n_hi, 1u));
-    for (uint32_t i = n_hi + tid; i < n2; i += blockDim.x) cand[i] = 0ull;
-    __syncthreads();
-    dev::bitonic_sort_desc(cand, n2);
-  }
-  for (uint32_t i = tid; i < n_hi; i += blockDim.x) out[i] = cand[i];
-  // ties at the k-th count, ascending id, from the Bitmap Counter
-  uint32_t n_tie = 0;
-  if (at_f >= 2 && n_hi < kq)
-    n_tie = collect_lanes<LOG2W, false>(bc, nwords_local, at_f - 1, kq - n_hi, obj_base,
-                                        out + n_hi, scratch);
-  for (uint32_t i = n_hi + n_tie + tid; i < kq; i += blockDim.x) out[i] = 0ull;
-
-  if (A.chunk_at && tid == 0) A.chunk_at[(unsigned long long)qi * A.n_groups + g] = at_f;
-  if (A.stats) {
-    unsigned long long gsum = dev::block_sum((unsigned long long)n_gate, scratch64);
-    unsigned long long isum = dev::block_sum((unsigned long long)n_ins, scratch64);
-    if (tid == 0) {
-      atomicAdd(&A.stats[0], gsum);
-      atomicAdd(&A.stats[1], isum);
-      if (!certified) atomicAdd(&A.stats[2], 1ull);
-      atomicAdd(&A.stats[4], 1ull);
-      if (s_flags[1]) atomicAdd(&A.stats[5], 1ull);
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Merge of the per-range top-k lists of each query (Sec. 3.4 merge, on device)
-// ---------------------------------------------------------------------------
-
-struct MergeArgs {
-  const unsigned long long* cand;
-  uint32_t n_sel;
-  const uint32_t* q_sel;
-  uint32_t n_groups;
-  uint32_t k;
-  const uint32_t* k_arr;
-  const uint32_t* bound;
-  uint32_t za_len;
-  uint32_t* ids;
-  uint32_t* counts;
-  uint32_t* n_valid;
-};
-
-constexpr uint32_t kMergeThreads = 256;
-
-__global__ void __launch_bounds__(kMergeThreads) merge_kernel(const MergeArgs M) {
-  extern __shared__ uint4 smem_raw[];
-  unsigned long long* buf = reinterpret_cast<unsigned long long*>(smem_raw);  // [next_pow2(k)]
-  uint32_t* hist = reinterpret_cast<uint32_t*>(buf + dev::next_pow2(M.k));    // [za_len]
-  __shared__ uint32_t s_t, s_ngt, s_r, s_n;
-  __shared__ uint32_t scratch[33];
-  const uint32_t tid = threadIdx.x;
-  for (uint32_t qi = blockIdx.x; qi < M.n_sel; qi += gridDim.x) {
-    const uint32_t q = M.q_sel ? M.q_sel[qi] : qi;
-    const uint32_t kq = M.k_arr ? M.k_arr[q] : M.k;
-    const uint32_t B = M.bound[q];
-    const unsigned long long* lists = M.cand + (unsigned long long)qi * M.n_groups * M.k;
-    for (uint32_t i = tid; i < B + 2; i += blockDim.x) hist[i] = 0;
-    if (tid == 0) s_n = 0;
-    __syncthreads();
-    const uint32_t total_c = M.n_groups * kq;
-    for (uint32_t i = tid; i < total_c; i += blockDim.x) {
-      unsigned long long key = lists[(i / kq) * M.k + (i % kq)];
-      if (key) atomicAdd(&hist[min(dev::key_count(key), B + 1)], 1u);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      uint32_t cum = 0, t = 1;
-      for (uint32_t v = B + 1; v >= 1; --v) {
-        if (cum + hist[v] >= kq) { t = v; break; }
-        cum += hist[v];
-      }
-      uint32_t ngt = 0;
-      for (uint32_t v = t + 1; v <= B + 1; ++v) ngt += hist[v];
-      s_t = t;
-      s_ngt = ngt;
-      s_r = min(kq - ngt, hist[t]);
-    }
-    __syncthreads();
-    const uint32_t t = s_t, ngt = s_ngt, r = s_r;
-    // every candidate above the k-th count
-    for (uint32_t i = tid; i < total_c; i += blockDim.x) {
-      unsigned long long key = lists[(i / kq) * M.k + (i % kq)];
-      if (key && dev::key_count(key) > t) buf[atomicAdd(&s_n, 1u)] = key;
-    }
-    __syncthreads();
-    const uint32_t n2 = dev::next_pow2(max(ngt, 1u));
-    for (uint32_t i = ngt + tid; i < n2; i += blockDim.x) buf[i] = 0ull;
-    __syncthreads();
-    dev::bitonic_sort_desc(buf, n2);
-    uint32_t* ids = M.ids + (unsigned long long)q * M.k;
-    uint32_t* cnt = M.counts + (unsigned long long)q * M.k;
-    for (uint32_t i = tid; i < ngt; i += blockDim.x) {
-      ids[i] = dev::key_id(buf[i]);
-      cnt[i] = dev::key_count(buf[i]);
-    }
-    // ties at the k-th count: range order = id order, each run ascending
-    const uint32_t per = (M.n_groups + blockDim.x - 1) / blockDim.x;
-    const uint32_t ga = min(M.n_groups, tid * per), gb = min(M.n_groups, ga + per);
-    uint32_t m = 0;
-    for (uint32_t gg = ga; gg < gb; ++gg)
-      for (uint32_t j = 0; j < kq; ++j) {
-        unsigned long long key = lists[(unsigned long long)gg * M.k + j];
-        m += key && dev::key_count(key) == t;
-      }
-    uint32_t tot;
-    uint32_t pos = dev::block_exclusive_scan(m, scratch, &tot);
-    for (uint32_t gg = ga; gg < gb && pos < r; ++gg)
-      for (uint32_t j = 0; j < kq && pos < r; ++j) {
-        unsigned long long key = lists[(unsigned long long)gg * M.k + j];
-        if (key && dev::key_count(key) == t) {
-          ids[ngt + pos] = dev::key_id(key);
-          cnt[ngt + pos] = t;
-          ++pos;
-        }
-      }
-    for (uint32_t i = ngt + r + tid; i < M.k; i += blockDim.x) {
-      ids[i] = 0xFFFFFFFFu;
-      cnt[i] = 0;
-    }
-    if (tid == 0) M.n_valid[q] = ngt + r;
-    __syncthreads();
-  }
-}
 
 // seeded search: queries whose result cannot be certified
 __global__ void verify_seeded_kernel(uint32_t n_queries, uint32_t k, const uint32_t* __restrict__ k_arr,
@@ -582,55 +65,6 @@ __global__ void verify_seeded_kernel(uint32_t n_queries, uint32_t k, const uint3
 }
 
 __global__ void add_stat_kernel(unsigned long long* stat, uint32_t v) { *stat += v; }
-
-__global__ void check_k_kernel(uint32_t n_queries, uint32_t k, const uint32_t* __restrict__ k_arr,
-                               uint32_t* bad) {
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n_queries; q += gridDim.x * blockDim.x)
-    if (k_arr[q] == 0 || k_arr[q] > k) atomicOr(bad, 1u);
-}
-
-struct Plan {
-  uint32_t log2w;
-  uint32_t unroll;
-  uint32_t block_shift;
-  uint32_t n_groups;
-  uint32_t ht_slots;
-  uint32_t threads;
-  uint32_t za_len;
-  size_t smem;
-};
-
-genie_status make_plan(const genie_index* idx, const genie_queries* qs, uint32_t k,
-                       const genie_search_opts* o, Plan* p) {
-  const uint32_t B = qs->max_bound;
-  p->log2w = B <= 15 ? 2u : (B <= 255 ? 3u : 4u);
-  uint32_t need = 0;
-  while (need < 31 && ((uint64_t)1 << need) < idx->n_objects) ++need;
-  uint32_t shift = 20 - p->log2w;  // 128 KB of Bitmap Counter
-  if (o && o->block_shift) shift = o->block_shift;
-  shift = std::min(shift, std::max(need, idx->chunk_shift));
-  shift = std::max(shift, idx->chunk_shift);
-  p->block_shift = shift;
-  p->n_groups = (uint32_t)(((uint64_t)idx->n_objects + (1ull << shift) - 1) >> shift);
-  uint32_t slots = (o && o->ht_slots) ? o->ht_slots : std::max(256u, dev::next_pow2(8 * k));
-  if (slots & (slots - 1)) return fail(GENIE_ERR_INVALID_ARG, "genie_search: ht_slots must be a power of two");
-  if (slots < 32) return fail(GENIE_ERR_INVALID_ARG, "genie_search: ht_slots must be >= 32");
-  p->ht_slots = slots;
-  p->threads = (o && o->threads) ? o->threads : 768u;
-  if (p->threads != 512 && p->threads != 768 && p->threads != 1024)
-    return fail(GENIE_ERR_INVALID_ARG, "genie_search: threads must be 512, 768 or 1024");
-  p->unroll = (o && o->unroll) ? o->unroll : (p->threads == 512 ? 4u : 2u);
-  if (p->threads == 512 ? (p->unroll != 4 && p->unroll != 8) : (p->unroll != 2 && p->unroll != 4))
-    return fail(GENIE_ERR_INVALID_ARG, "genie_search: unroll must be 2 or 4 (768 or 1024 threads), 4 or 8 (512)");
-  p->za_len = B + 2;
-  p->smem = scan_smem_bytes(p->log2w, shift, slots, p->za_len, k);
-  int dev = 0, max_smem = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (p->smem + 1024 > (size_t)max_smem)
-    return fail(GENIE_ERR_INVALID_ARG, "genie_search: block_shift / ht_slots need more shared memory than a block has");
-  return GENIE_OK;
-}
 
 template <int LOG2W, int U, int THREADS>
 cudaError_t launch_scan(const ScanArgs& a, const Plan& p, cudaStream_t s) {

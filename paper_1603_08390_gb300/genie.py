@@ -32,7 +32,8 @@ EXPORTED = (
     "genie_queries_destroy", "genie_queries_get_info", "genie_queries_export", "genie_search",
     "genie_search_noalloc", "genie_mlp_num_params", "genie_mlp_create", "genie_mlp_destroy",
     "genie_mlp_set_params", "genie_mlp_get_params", "genie_mlp_forward", "genie_mlp_gradients",
-    "genie_mlp_adam_step", "genie_mlp_train", "genie_mlp_seeds",
+    "genie_mlp_adam_step", "genie_mlp_train", "genie_mlp_seeds", "genie_autotune",
+    "genie_batch_create", "genie_batch_get_info", "genie_batch_destroy", "genie_batch_run",
 )
 
 
@@ -52,6 +53,13 @@ class IndexInfo(ctypes.Structure):
 class QueriesInfo(ctypes.Structure):
     _fields_ = [("n_queries", ctypes.c_uint32), ("max_bound", ctypes.c_uint32),
                 ("n_keywords", ctypes.c_uint64), ("n_entries", ctypes.c_uint64)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("block_shift", ctypes.c_uint32), ("threads", ctypes.c_uint32),
+                ("unroll", ctypes.c_uint32), ("ht_slots", ctypes.c_uint32),
+                ("blocks", ctypes.c_uint32), ("tuned_ms", ctypes.c_float),
+                ("from_cache", ctypes.c_uint32)]
 
 
 class SearchOpts(ctypes.Structure):
@@ -117,6 +125,16 @@ def load(path: Optional[str] = None):
         lib.genie_mlp_adam_step.argtypes = [vp, f32, vp]
         lib.genie_mlp_train.argtypes = [vp, vp, vp, u32, u32, u32, f32, ctypes.POINTER(f32), vp]
         lib.genie_mlp_seeds.argtypes = [vp, vp, f32, vp, vp]
+        lib.genie_autotune.argtypes = [vp, vp, u32, ctypes.c_char_p, ctypes.POINTER(BatchOpts)]
+        lib.genie_batch_create.argtypes = [vp, u32, u32, u32, ctypes.POINTER(BatchOpts),
+                                           ctypes.POINTER(vp)]
+        lib.genie_batch_get_info.argtypes = [vp, ctypes.POINTER(BatchOpts)]
+        lib.genie_batch_destroy.argtypes = [vp]
+        lib.genie_batch_destroy.restype = None
+        lib.genie_batch_run.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        for name in ("genie_autotune", "genie_batch_create", "genie_batch_get_info",
+                     "genie_batch_run"):
+            getattr(lib, name).restype = st
         for name in ("genie_mlp_create", "genie_mlp_set_params", "genie_mlp_get_params",
                      "genie_mlp_forward", "genie_mlp_gradients", "genie_mlp_adam_step",
                      "genie_mlp_train", "genie_mlp_seeds"):
@@ -328,3 +346,45 @@ class MLP:
     def seeds(self, queries: Queries, margin: float, d_seed, stream=None):
         _check(load().genie_mlp_seeds(self.handle, queries.handle, margin, _ptr(d_seed),
                                       _stream(stream)), load())
+
+
+def genie_autotune(index: Index, sample: Queries, k: int, cache_path: Optional[str] = None) -> BatchOpts:
+    lib = load()
+    out = BatchOpts()
+    _check(lib.genie_autotune(index.handle, sample.handle, k,
+                              cache_path.encode() if cache_path else None, ctypes.byref(out)), lib)
+    return out
+
+
+class Batch:
+    """Owning wrapper of a ``genie_batch*`` (persistent, graph-captured plan)."""
+
+    def __init__(self, index: Index, max_queries: int, max_bound: int, k: int,
+                 opts: Optional[BatchOpts] = None):
+        lib = load()
+        out = ctypes.c_void_p()
+        _check(lib.genie_batch_create(index.handle, max_queries, max_bound, k,
+                                      ctypes.byref(opts) if opts is not None else None,
+                                      ctypes.byref(out)), lib)
+        self.handle = out.value
+        self.index = index
+        self.k = k
+        info = BatchOpts()
+        _check(lib.genie_batch_get_info(self.handle, ctypes.byref(info)), lib)
+        self.info = info
+
+    def run(self, queries: Queries, d_ids, d_counts, d_n_valid, d_k=None, stream=None):
+        lib = load()
+        _check(lib.genie_batch_run(self.handle, queries.handle, _ptr(d_k), _ptr(d_ids),
+                                   _ptr(d_counts), _ptr(d_n_valid), _stream(stream)), lib)
+
+    def close(self):
+        if self.handle:
+            load().genie_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
