@@ -48,12 +48,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["genie", "reference"], default="genie")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["lsh1m", "lsh4m-learned", "sets4m-batched"],
+    ap.add_argument("--workload", choices=["lsh1m", "lsh4m-learned", "sets4m-batched", "serving"],
                     default="lsh1m",
                     help="lsh1m: the headline batch; lsh4m-learned: plain vs learned-seed "
                          "search on 4M objects / 4096 queries (k=100); sets4m-batched: plain "
                          "launch vs the persistent graph-captured batch on 4M Zipf sets / 8192 "
-                         "queries (k=10)")
+                         "queries (k=10); serving: continuous-batching server on 8M x 64 Zipf "
+                         "sets, Poisson arrivals at a swept rate, k in {1, 10, 100}")
     ap.add_argument("--queries", type=int, default=N_QUERIES,
                     help="queries per batch (the workload is defined at 1024; smaller "
                          "values are for profiling captures)")
@@ -516,6 +517,71 @@ def run_batched(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, rank, world, local):
+    """Continuous-batching server: saturation throughput and p50/p99 latency
+    under Poisson arrivals at fractions of it (8M x 64 Zipf sets)."""
+    import torch
+    import synth
+    from paper_1603_08390_gb300 import _build, genie, runner
+
+    _build.build()
+    torch.cuda.set_device(local)
+    w = synth.sets(8_000_000, (64, 64), 1 << 22, 16, (8, 512), 10, config=5)  # the objects
+    idx = runner.build_index(w)
+    n_req = 4000
+    q_off, q_kw, ks, _ = synth.serving_requests(n_req, 1.0, config=5)
+    budget = 512 * w.n_objects  # counter bytes of 512 queries at 8 bits per object
+    opts = genie.ServerOpts(bc_budget_bytes=budget, bits_per_object=8, max_batch=256,
+                            max_query_keywords=512, k_max=100, streams=2)
+    srv = genie.Server(idx, opts)
+    # warm-up, then saturation: every request at t = 0
+    srv.replay(q_off[:201] - q_off[0], q_kw[:q_off[200]], ks[:200], np.zeros(200))
+    t0 = time.perf_counter()
+    lat0, ids0, _, nv0 = srv.replay(q_off, q_kw, ks, np.zeros(n_req))
+    sat_s = time.perf_counter() - t0
+    sat_qps = n_req / sat_s
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    sweep = []
+    rng = np.random.default_rng(123)
+    for frac in (0.25, 0.5, 0.75, 0.9):
+        rate = frac * sat_qps
+        arrival = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        t1 = time.perf_counter()
+        lat, ids, _, nv = srv.replay(q_off, q_kw, ks, arrival)
+        wall = time.perf_counter() - t1
+        same = bool(np.array_equal(nv, nv0) and all(
+            np.array_equal(ids[i, :nv[i]], ids0[i, :nv0[i]]) for i in range(n_req)))
+        sweep.append({"offered_qps": rate, "achieved_qps": n_req / wall,
+                      "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                      "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                      "mean_ms": float(lat.mean() * 1e3), "results_same_as_saturation": same})
+    clk = clocks.stop()
+    st = srv.stats()
+    qsz = np.diff(q_off.astype(np.int64))
+    line = {
+        "metric": METRIC, "value": sat_qps, "unit": UNIT, "n_gpus": 1, "steps": len(sweep) + 1,
+        "warmup": 1, "ms_per_step": sat_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic", "impl": "genie-serving",
+        "config": {"workload": "serving: 8,000,000 objects x 64 Zipf(1.1) keywords over 2^22, "
+                               "requests of 8-512 keywords, k uniform in {1, 10, 100}, Poisson "
+                               "arrivals; admission by Bitmap-Counter bytes (8 bits per object "
+                               "per query), budget = 512 queries",
+                   "n_objects": w.n_objects, "n_requests": n_req,
+                   "mean_request_keywords": float(qsz.mean()), "streams": 2, "max_batch": 256},
+        "saturation": {"qps": sat_qps, "p50_ms": float(np.percentile(lat0, 50) * 1e3),
+                       "p99_ms": float(np.percentile(lat0, 99) * 1e3)},
+        "sweep": sweep,
+        "server": {"launches": int(st.launches), "queries": int(st.queries),
+                   "mean_batch": float(st.queries) / max(1, st.launches),
+                   "deferred_admissions": int(st.deferred_admissions),
+                   "max_queries_in_flight": int(st.max_queries_in_flight)},
+        "clocks": clk,
+    }
+    srv.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup()
@@ -527,6 +593,9 @@ def main():
     elif args.workload == "sets4m-batched":
         if rank == 0:
             run_batched(args, rank, world, local)
+    elif args.workload == "serving":
+        if rank == 0:
+            run_serving(args, rank, world, local)
     else:
         run_genie(args, rank, world, local)
     if world > 1:

@@ -293,6 +293,88 @@ genie_status genie_batch_run(genie_batch* batch, const genie_queries* queries, c
                              genie_stream stream);
 
 /* ------------------------------------------------------------------------ */
+/* Serving loop with continuous batching (not in the paper)                  */
+/* ------------------------------------------------------------------------ */
+/*
+ * A server keeps the index resident and answers requests (host keyword
+ * multisets with their own k) submitted at any time.  A worker thread keeps up
+ * to `streams` batches in flight on their own CUDA streams; whenever one
+ * finishes, the queued requests that fit are admitted into the next batch,
+ * so requests arriving while others run overlap with them on the device.
+ * Admission is by counter memory: each in-flight query holds n_objects x
+ * bits / 8 bytes of the budget (the Bitmap Counter of Sec. 3.3.1) until its
+ * batch completes.  Results equal genie_search's for the same query.  Device
+ * memory is allocated once at creation; the loop itself neither allocates
+ * nor synchronises per batch.
+ */
+typedef struct genie_server genie_server;
+
+typedef struct {
+  uint64_t bc_budget_bytes;    /* counter bytes of all in-flight queries (default 8 GiB) */
+  uint32_t bits_per_object;    /* counter bits charged per object per query (0 = the
+                                  query's counter width: 4, 8 or 16) */
+  uint32_t max_batch;          /* queries per launch (default 256) */
+  uint32_t max_query_keywords; /* keywords per request (default 4096) */
+  uint32_t k_max;              /* largest k of a request (default 100) */
+  uint32_t streams;            /* batches in flight, 1..8 (default 2) */
+  uint32_t queue_capacity;     /* queued requests (default 65536) */
+} genie_server_opts;
+
+typedef struct {
+  uint64_t tag;        /* the caller's tag */
+  uint32_t k;          /* the request's k */
+  uint32_t n_valid;    /* results written (ranks past it are padding) */
+  double t_submit;     /* genie_server_clock() at submission */
+  double t_done;       /* genie_server_clock() when the worker saw the batch finish */
+} genie_result_info;
+
+typedef struct {
+  uint64_t launches;               /* batches launched */
+  uint64_t queries;                /* queries launched */
+  uint64_t deferred_admissions;    /* requests that waited for counter budget */
+  uint64_t max_queries_in_flight;  /* largest number of queries on the device at once */
+  uint64_t pending;                /* queued now */
+  uint64_t reserved_bytes;         /* counter budget held now */
+} genie_server_stats;
+
+/* Monotonic clock of the server, in seconds. */
+double genie_server_clock(void);
+
+/* Start a server on `index` (which must outlive it).  opts may be NULL. */
+genie_status genie_server_create(const genie_index* index, const genie_server_opts* opts,
+                                 genie_server** out);
+
+/* Finish all admitted work, stop the worker and free the server. */
+void genie_server_destroy(genie_server* server);
+
+/* Queue one request: h_kw[n_kw] host keywords (< vocab), 1 <= k <= k_max.
+ * The keywords are copied.  GENIE_ERR_CAPACITY if the queue is full or one
+ * query's counters exceed the whole budget; INVALID_ARG for bad input. */
+genie_status genie_server_submit(genie_server* server, const uint32_t* h_kw, uint32_t n_kw,
+                                 uint32_t k, uint64_t tag);
+
+/* Completed requests, oldest first: up to max_results, waiting at most
+ * timeout_us for the first.  h_ids / h_counts hold max_results rows of
+ * k_max entries (the first k of row j are request j's results). */
+genie_status genie_server_poll(genie_server* server, uint32_t max_results, uint32_t timeout_us,
+                               genie_result_info* h_info, uint32_t* h_ids, uint32_t* h_counts,
+                               uint32_t* n_out);
+
+genie_status genie_server_get_stats(genie_server* server, genie_server_stats* out);
+
+/* Open-loop load replay on an otherwise idle server: request i (keywords
+ * h_q_kw[h_q_off[i] .. h_q_off[i+1]-1], k = h_k[i]) is submitted h_arrival_s[i]
+ * seconds after the call starts; the call returns when all n completed.
+ * h_latency_s[i] = completion time - scheduled arrival; results go to row i
+ * of h_ids / h_counts ([n x k_max]) and h_n_valid[i].  GENIE_ERR_TIMEOUT if
+ * requests are still open after timeout_ms. */
+genie_status genie_server_replay(genie_server* server, const uint32_t* h_q_off,
+                                 const uint32_t* h_q_kw, const uint32_t* h_k,
+                                 const double* h_arrival_s, uint32_t n, uint32_t timeout_ms,
+                                 double* h_latency_s, uint32_t* h_ids, uint32_t* h_counts,
+                                 uint32_t* h_n_valid);
+
+/* ------------------------------------------------------------------------ */
 /* k-th-count predictor: a learned AuditThreshold seed (not in the paper)    */
 /* ------------------------------------------------------------------------ */
 /*

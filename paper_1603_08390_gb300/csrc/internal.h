@@ -19,6 +19,13 @@ void launch_exclusive_scan(uint32_t* v, uint32_t n, uint32_t* total, cudaStream_
 
 inline cudaStream_t as_stream(genie_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Search over caller-owned device query arrays (search.cu).
+size_t search_scratch_bytes(const genie_index* idx, uint32_t max_bound, uint32_t n, uint32_t k);
+genie_status search_raw(const genie_index* idx, const uint32_t* q_off, const uint32_t* q_kw,
+                        const uint32_t* bound, uint32_t n, uint32_t max_bound, uint32_t k,
+                        const uint32_t* d_k, unsigned long long* cand, size_t cand_bytes,
+                        uint32_t* ids, uint32_t* counts, uint32_t* n_valid, cudaStream_t s);
+
 }  // namespace genie
 
 #define GENIE_CUDA_TRY(expr)                                           \

@@ -145,6 +145,45 @@ cudaError_t run_pass(const genie_index* idx, const genie_queries* qs, uint32_t k
 }  // namespace
 }  // namespace genie
 
+namespace genie {
+
+// Search over caller-owned device query arrays (no handle, no allocation, no
+// synchronisation): q_off [n+1], q_kw, bound [n] (the count bounds, at most
+// max_bound), cand = scratch of search_scratch_bytes().  Used by host
+// runtimes that keep their own buffers (the serving loop).
+size_t search_scratch_bytes(const genie_index* idx, uint32_t max_bound, uint32_t n, uint32_t k) {
+  genie_queries view;
+  view.index = idx;
+  view.max_bound = max_bound;
+  Plan p;
+  if (make_plan(idx, &view, k, nullptr, &p) != GENIE_OK) return 0;
+  return (size_t)n * p.n_groups * k * 8;
+}
+
+genie_status search_raw(const genie_index* idx, const uint32_t* q_off, const uint32_t* q_kw,
+                        const uint32_t* bound, uint32_t n, uint32_t max_bound, uint32_t k,
+                        const uint32_t* d_k, unsigned long long* cand, size_t cand_bytes,
+                        uint32_t* ids, uint32_t* counts, uint32_t* n_valid, cudaStream_t s) {
+  genie_queries view;
+  view.index = idx;
+  view.n_queries = n;
+  view.max_bound = max_bound;
+  view.q_off = const_cast<uint32_t*>(q_off);
+  view.q_kw = const_cast<uint32_t*>(q_kw);
+  view.bound = const_cast<uint32_t*>(bound);
+  Plan p;
+  genie_status st = make_plan(idx, &view, k, nullptr, &p);
+  if (st != GENIE_OK) return st;
+  if ((size_t)n * p.n_groups * k * 8 > cand_bytes)
+    return fail(GENIE_ERR_CAPACITY, "search_raw: scratch too small");
+  cudaError_t e = run_pass(idx, &view, k, d_k, nullptr, nullptr, n, p, nullptr, cand, ids, counts,
+                           n_valid, s);
+  if (e != cudaSuccess) return fail_cuda(e, "search_raw");
+  return GENIE_OK;
+}
+
+}  // namespace genie
+
 using namespace genie;
 
 extern "C" genie_status genie_search(const genie_index* index, const genie_queries* queries,

@@ -34,6 +34,8 @@ EXPORTED = (
     "genie_mlp_set_params", "genie_mlp_get_params", "genie_mlp_forward", "genie_mlp_gradients",
     "genie_mlp_adam_step", "genie_mlp_train", "genie_mlp_seeds", "genie_autotune",
     "genie_batch_create", "genie_batch_get_info", "genie_batch_destroy", "genie_batch_run",
+    "genie_server_clock", "genie_server_create", "genie_server_destroy", "genie_server_submit",
+    "genie_server_poll", "genie_server_get_stats", "genie_server_replay",
 )
 
 
@@ -60,6 +62,25 @@ class BatchOpts(ctypes.Structure):
                 ("unroll", ctypes.c_uint32), ("ht_slots", ctypes.c_uint32),
                 ("blocks", ctypes.c_uint32), ("tuned_ms", ctypes.c_float),
                 ("from_cache", ctypes.c_uint32)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("bc_budget_bytes", ctypes.c_uint64), ("bits_per_object", ctypes.c_uint32),
+                ("max_batch", ctypes.c_uint32), ("max_query_keywords", ctypes.c_uint32),
+                ("k_max", ctypes.c_uint32), ("streams", ctypes.c_uint32),
+                ("queue_capacity", ctypes.c_uint32)]
+
+
+class ResultInfo(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("k", ctypes.c_uint32), ("n_valid", ctypes.c_uint32),
+                ("t_submit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("queries", ctypes.c_uint64),
+                ("deferred_admissions", ctypes.c_uint64),
+                ("max_queries_in_flight", ctypes.c_uint64), ("pending", ctypes.c_uint64),
+                ("reserved_bytes", ctypes.c_uint64)]
 
 
 class SearchOpts(ctypes.Structure):
@@ -132,8 +153,19 @@ def load(path: Optional[str] = None):
         lib.genie_batch_destroy.argtypes = [vp]
         lib.genie_batch_destroy.restype = None
         lib.genie_batch_run.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        lib.genie_server_clock.restype = ctypes.c_double
+        lib.genie_server_clock.argtypes = []
+        lib.genie_server_create.argtypes = [vp, ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
+        lib.genie_server_destroy.argtypes = [vp]
+        lib.genie_server_destroy.restype = None
+        lib.genie_server_submit.argtypes = [vp, vp, u32, u32, u64]
+        lib.genie_server_poll.argtypes = [vp, u32, u32, ctypes.POINTER(ResultInfo), vp, vp,
+                                          ctypes.POINTER(u32)]
+        lib.genie_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        lib.genie_server_replay.argtypes = [vp, vp, vp, vp, vp, u32, u32, vp, vp, vp, vp]
         for name in ("genie_autotune", "genie_batch_create", "genie_batch_get_info",
-                     "genie_batch_run"):
+                     "genie_batch_run", "genie_server_create", "genie_server_submit",
+                     "genie_server_poll", "genie_server_get_stats", "genie_server_replay"):
             getattr(lib, name).restype = st
         for name in ("genie_mlp_create", "genie_mlp_set_params", "genie_mlp_get_params",
                      "genie_mlp_forward", "genie_mlp_gradients", "genie_mlp_adam_step",
@@ -381,6 +413,76 @@ class Batch:
     def close(self):
         if self.handle:
             load().genie_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owning wrapper of a ``genie_server*`` (continuous-batching serving loop).
+    Host arrays are numpy arrays."""
+
+    def __init__(self, index: Index, opts: Optional[ServerOpts] = None):
+        lib = load()
+        out = ctypes.c_void_p()
+        _check(lib.genie_server_create(index.handle, ctypes.byref(opts) if opts is not None else None,
+                                       ctypes.byref(out)), lib)
+        self.handle = out.value
+        self.index = index
+        self.k_max = opts.k_max if (opts is not None and opts.k_max) else 100
+
+    @staticmethod
+    def clock() -> float:
+        return load().genie_server_clock()
+
+    def submit(self, kw, k: int, tag: int):
+        import numpy as np
+        kw = np.ascontiguousarray(kw, dtype=np.uint32)
+        _check(load().genie_server_submit(self.handle, kw.ctypes.data_as(ctypes.c_void_p), len(kw),
+                                          k, tag), load())
+
+    def poll(self, max_results: int = 64, timeout_us: int = 0):
+        """List of (info, ids, counts) for completed requests."""
+        import numpy as np
+        info = (ResultInfo * max(1, max_results))()
+        ids = np.empty((max(1, max_results), self.k_max), dtype=np.uint32)
+        cnt = np.empty_like(ids)
+        n = ctypes.c_uint32(0)
+        _check(load().genie_server_poll(self.handle, max_results, timeout_us, info,
+                                        ids.ctypes.data_as(ctypes.c_void_p),
+                                        cnt.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)), load())
+        return [(info[j], ids[j, :info[j].k].copy(), cnt[j, :info[j].k].copy())
+                for j in range(n.value)]
+
+    def stats(self) -> ServerStats:
+        st = ServerStats()
+        _check(load().genie_server_get_stats(self.handle, ctypes.byref(st)), load())
+        return st
+
+    def replay(self, q_off, q_kw, ks, arrival_s, timeout_ms: int = 600000):
+        """Open-loop replay; returns (latency_s, ids, counts, n_valid)."""
+        import numpy as np
+        q_off = np.ascontiguousarray(q_off, dtype=np.uint32)
+        q_kw = np.ascontiguousarray(q_kw, dtype=np.uint32)
+        ks = np.ascontiguousarray(ks, dtype=np.uint32)
+        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        n = len(ks)
+        lat = np.empty(n, dtype=np.float64)
+        ids = np.empty((n, self.k_max), dtype=np.uint32)
+        cnt = np.empty_like(ids)
+        nv = np.empty(n, dtype=np.uint32)
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(load().genie_server_replay(self.handle, p(q_off), p(q_kw), p(ks), p(arr), n,
+                                          timeout_ms, p(lat), p(ids), p(cnt), p(nv)), load())
+        return lat, ids, cnt, nv
+
+    def close(self):
+        if self.handle:
+            load().genie_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
