@@ -321,3 +321,18 @@ def test_full_zipf_4m_sampled():
     res, idx, qs = run(w)
     rows, ref = _sampled(w, 12, 1)
     assert_same(res, ref, rows)
+
+
+def test_full_lsh_4m_sampled():
+    w = synth.config(4)
+    res, idx, qs = run(w)
+    rows, ref = _sampled(w, 8, 2)
+    assert_same(res, ref, rows)
+
+
+def test_full_serving_index_8m_per_query_k_sampled():
+    w = synth.config(5)
+    res, idx, qs = run(w)
+    assert qs.max_bound <= 64  # 8-bit counters
+    rows, ref = _sampled(w, 12, 3)
+    assert_same(res, ref, rows)
