@@ -217,10 +217,21 @@ typedef struct {
    * caller can time that kernel alone with cudaEventElapsedTime. */
   void* scan_event_begin;
   void* scan_event_end;
+  /* GENIE_SEARCH_* flags (0 = defaults). */
+  uint32_t flags;
 } genie_search_opts;
 
+/* Each object range of a query starts its AuditThreshold at 1 (or at the
+ * seed) instead of at the largest k-th count of the query's ranges already
+ * finished.  Results are the same either way; this exposes the per-range
+ * AuditThreshold of Theorem 3.1 in d_chunk_at. */
+#define GENIE_SEARCH_PER_RANGE_AT 1u
+
 /*
- * Top-k of every query.
+ * Top-k of every query.  By default the ranges of a query share what they
+ * learn: a range starts its AuditThreshold at the largest k-th count of the
+ * query's ranges finished so far, which is never above the query's k-th
+ * count, so no top-k object is skipped (see GENIE_SEARCH_PER_RANGE_AT).
  *   k          1 .. GENIE_MAX_K: result slots per query (row stride).
  *   d_k        NULL, or [n_queries] uint32 device per-query k_q in 1..k.
  *   opts       NULL for defaults.

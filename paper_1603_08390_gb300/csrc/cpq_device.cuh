@@ -39,6 +39,11 @@ struct ScanArgs {
   unsigned long long* cand;  // [n_sel][n_groups][k]
   uint32_t* chunk_at;        // [n_sel][n_groups] or NULL
   unsigned long long* stats;
+  // [n_sel] or NULL: the largest k-th count of the query's ranges finished so
+  // far.  The k-th count of a range is at most the query's k-th count (the
+  // k-th largest of a subset never exceeds that of the whole set), so a range
+  // may start its AuditThreshold there without losing any top-k object.
+  uint32_t* at_hint;
 };
 
 constexpr uint32_t kMaxProbe = 32;   // hash-table probes before an insert gives up
@@ -243,6 +248,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     for (uint32_t i = tid; i < B + 2; i += blockDim.x) za[i] = 0;
     if (tid == 0) {
       uint32_t s0 = A.seed ? A.seed[q] : 1u;
+      if (A.at_hint) s0 = max(s0, vld(&A.at_hint[qi]));
       s_at = max(1u, min(s0, B + 1));
       s_flags[0] = 0;
       s_flags[1] = 0;
@@ -437,6 +443,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   for (uint32_t i = n_hi + n_tie + tid; i < kq; i += blockDim.x) out[i] = 0ull;
 
   if (A.chunk_at && tid == 0) A.chunk_at[(unsigned long long)qi * A.n_groups + g] = at_f;
+  if (A.at_hint && tid == 0 && at_f >= 2) atomicMax(&A.at_hint[qi], at_f - 1);
   if (A.stats) {
     unsigned long long gsum = dev::block_sum((unsigned long long)n_gate, scratch64);
     unsigned long long isum = dev::block_sum((unsigned long long)n_ins, scratch64);

@@ -24,7 +24,8 @@ size_t search_scratch_bytes(const genie_index* idx, uint32_t max_bound, uint32_t
 genie_status search_raw(const genie_index* idx, const uint32_t* q_off, const uint32_t* q_kw,
                         const uint32_t* bound, uint32_t n, uint32_t max_bound, uint32_t k,
                         const uint32_t* d_k, unsigned long long* cand, size_t cand_bytes,
-                        uint32_t* ids, uint32_t* counts, uint32_t* n_valid, cudaStream_t s);
+                        uint32_t* at_hint, uint32_t* ids, uint32_t* counts, uint32_t* n_valid,
+                        cudaStream_t s);
 
 }  // namespace genie
 

@@ -91,10 +91,11 @@ cudaError_t dispatch_scan(const ScanArgs& a, const Plan& p, cudaStream_t s) {
                       : dispatch_width<4>(a, p, s);
 }
 
+// at_hint: [n_sel] zeroed device words shared by a query's ranges, or NULL
 cudaError_t run_pass(const genie_index* idx, const genie_queries* qs, uint32_t k, const uint32_t* d_k,
                      const uint32_t* seed, const uint32_t* sel, uint32_t n_sel, const Plan& p,
-                     const genie_search_opts* o, unsigned long long* cand, uint32_t* ids,
-                     uint32_t* counts, uint32_t* n_valid, cudaStream_t s) {
+                     const genie_search_opts* o, unsigned long long* cand, uint32_t* at_hint,
+                     uint32_t* ids, uint32_t* counts, uint32_t* n_valid, cudaStream_t s) {
   ScanArgs a;
   a.kw_off = idx->kw_off;
   a.post_ids = idx->post_ids;
@@ -118,6 +119,7 @@ cudaError_t run_pass(const genie_index* idx, const genie_queries* qs, uint32_t k
   a.cand = cand;
   a.chunk_at = (o && !sel) ? o->d_chunk_at : nullptr;
   a.stats = o ? o->d_stats : nullptr;
+  a.at_hint = at_hint;
   const bool timed = o && !sel && o->scan_event_begin && o->scan_event_end;
   if (timed) cudaEventRecord((cudaEvent_t)o->scan_event_begin, s);
   cudaError_t e = dispatch_scan(a, p, s);
@@ -163,7 +165,8 @@ size_t search_scratch_bytes(const genie_index* idx, uint32_t max_bound, uint32_t
 genie_status search_raw(const genie_index* idx, const uint32_t* q_off, const uint32_t* q_kw,
                         const uint32_t* bound, uint32_t n, uint32_t max_bound, uint32_t k,
                         const uint32_t* d_k, unsigned long long* cand, size_t cand_bytes,
-                        uint32_t* ids, uint32_t* counts, uint32_t* n_valid, cudaStream_t s) {
+                        uint32_t* at_hint, uint32_t* ids, uint32_t* counts, uint32_t* n_valid,
+                        cudaStream_t s) {
   genie_queries view;
   view.index = idx;
   view.n_queries = n;
@@ -176,8 +179,10 @@ genie_status search_raw(const genie_index* idx, const uint32_t* q_off, const uin
   if (st != GENIE_OK) return st;
   if ((size_t)n * p.n_groups * k * 8 > cand_bytes)
     return fail(GENIE_ERR_CAPACITY, "search_raw: scratch too small");
-  cudaError_t e = run_pass(idx, &view, k, d_k, nullptr, nullptr, n, p, nullptr, cand, ids, counts,
-                           n_valid, s);
+  cudaError_t e = at_hint ? cudaMemsetAsync(at_hint, 0, (size_t)n * 4, s) : cudaSuccess;
+  if (e == cudaSuccess)
+    e = run_pass(idx, &view, k, d_k, nullptr, nullptr, n, p, nullptr, cand, at_hint, ids, counts,
+                 n_valid, s);
   if (e != cudaSuccess) return fail_cuda(e, "search_raw");
   return GENIE_OK;
 }
@@ -205,7 +210,7 @@ extern "C" genie_status genie_search(const genie_index* index, const genie_queri
   unsigned long long* cand = nullptr;
   uint32_t* aux = nullptr;  // [0] flags, [1] rerun count, [2..] rerun list
   GENIE_CUDA_TRY(cudaMallocAsync((void**)&cand, cand_bytes, s));
-  cudaError_t e = cudaMallocAsync((void**)&aux, (uint64_t)(Q + 2) * 4, s);
+  cudaError_t e = cudaMallocAsync((void**)&aux, (uint64_t)(2 * Q + 2) * 4, s);
   if (e != cudaSuccess) {
     cudaFreeAsync(cand, s);
     return fail_cuda(e, "cudaMallocAsync");
@@ -226,7 +231,12 @@ extern "C" genie_status genie_search(const genie_index* index, const genie_queri
     if (bad) { release(); return fail(GENIE_ERR_INVALID_ARG, "genie_search: a per-query k is 0 or larger than k"); }
   }
   const uint32_t* seed = opts ? opts->d_seed : nullptr;
-  e = run_pass(index, queries, k, d_k, seed, nullptr, Q, p, opts, cand, d_ids, d_counts, d_n_valid, s);
+  const bool share = !(opts && (opts->flags & GENIE_SEARCH_PER_RANGE_AT));
+  uint32_t* hint = share ? aux + 2 + Q : nullptr;  // [Q]: largest k-th count of finished ranges
+  e = hint ? cudaMemsetAsync(hint, 0, (size_t)Q * 4, s) : cudaSuccess;
+  if (e == cudaSuccess)
+    e = run_pass(index, queries, k, d_k, seed, nullptr, Q, p, opts, cand, hint, d_ids, d_counts,
+                 d_n_valid, s);
   if (e == cudaSuccess && seed) {
     // verify-and-rerun: certified iff s = 1 or the k-th merged count >= s
     uint32_t n_rerun = 0;
@@ -239,8 +249,10 @@ extern "C" genie_status genie_search(const genie_index* index, const genie_queri
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess && n_rerun > 0) {
       if (opts && opts->d_stats) add_stat_kernel<<<1, 1, 0, s>>>(opts->d_stats + 3, n_rerun);
-      e = run_pass(index, queries, k, d_k, nullptr, aux + 2, n_rerun, p, opts, cand, d_ids,
-                   d_counts, d_n_valid, s);
+      e = hint ? cudaMemsetAsync(hint, 0, (size_t)n_rerun * 4, s) : cudaSuccess;
+      if (e == cudaSuccess)
+        e = run_pass(index, queries, k, d_k, nullptr, aux + 2, n_rerun, p, opts, cand, hint, d_ids,
+                     d_counts, d_n_valid, s);
     }
   }
   release();
@@ -315,10 +327,11 @@ extern "C" genie_status genie_search_noalloc(const genie_index* index, const gen
   if (st != GENIE_OK) return st;
   if (opts && opts->h_blocks_per_query) *opts->h_blocks_per_query = p.n_groups;
   const uint64_t cand_bytes = (uint64_t)queries->n_queries * p.n_groups * k * 8;
-  if (cand_bytes > kNoAllocScratchBytes - kNoAllocStatusBytes)
+  const uint64_t hint_bytes = (uint64_t)queries->n_queries * 4;
+  if (cand_bytes + hint_bytes > kNoAllocScratchBytes - kNoAllocStatusBytes)
     return fail(GENIE_ERR_CAPACITY,
-                "genie_search_noalloc: queries x object ranges x k x 8 bytes = " +
-                    std::to_string(cand_bytes) + " exceeds the fixed scratch of " +
+                "genie_search_noalloc: queries x (object ranges x k x 8 + 4) bytes = " +
+                    std::to_string(cand_bytes + hint_bytes) + " exceeds the fixed scratch of " +
                     std::to_string(kNoAllocScratchBytes - kNoAllocStatusBytes) +
                     " bytes; use fewer queries per call or genie_search");
   void* base = nullptr;
@@ -337,8 +350,12 @@ extern "C" genie_status genie_search_noalloc(const genie_index* index, const gen
     if (bad) return fail(GENIE_ERR_INVALID_ARG, "genie_search_noalloc: a per-query k is 0 or larger than k");
   }
   // the scan kernel writes every candidate slot the merge reads, so the
-  // candidate lists need no clearing between calls
-  cudaError_t e = run_pass(index, queries, k, d_k, nullptr, nullptr, Q, p, opts, cand, d_ids,
+  // candidate lists need no clearing between calls; the shared k-th counts do
+  const bool share = !(opts && (opts->flags & GENIE_SEARCH_PER_RANGE_AT));
+  uint32_t* hint = share ? reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(base) + cand_bytes)
+                         : nullptr;
+  if (hint) GENIE_CUDA_TRY(cudaMemsetAsync(hint, 0, hint_bytes, s));
+  cudaError_t e = run_pass(index, queries, k, d_k, nullptr, nullptr, Q, p, opts, cand, hint, d_ids,
                            d_counts, d_n_valid, s);
   if (e != cudaSuccess) return fail_cuda(e, "genie_search_noalloc");
   return GENIE_OK;

@@ -24,6 +24,7 @@ GENIE_ERR_CAPACITY = 4
 GENIE_ERR_TIMEOUT = 5
 GENIE_MAX_K = 1024
 GENIE_MAX_BOUND = 4095
+GENIE_SEARCH_PER_RANGE_AT = 1
 N_FEATURES = 64
 
 EXPORTED = (
@@ -89,7 +90,8 @@ class SearchOpts(ctypes.Structure):
                 ("unroll", ctypes.c_uint32),
                 ("d_chunk_at", ctypes.c_void_p), ("d_stats", ctypes.c_void_p),
                 ("h_blocks_per_query", ctypes.POINTER(ctypes.c_uint32)),
-                ("scan_event_begin", ctypes.c_void_p), ("scan_event_end", ctypes.c_void_p)]
+                ("scan_event_begin", ctypes.c_void_p), ("scan_event_end", ctypes.c_void_p),
+                ("flags", ctypes.c_uint32)]
 
 
 _LIB = None
@@ -295,13 +297,15 @@ def genie_queries_export(queries: Queries, d_bound=None, d_entries=None, d_featu
 
 
 def make_opts(d_seed=None, block_shift: int = 0, threads: int = 0, ht_slots: int = 0,
-              d_chunk_at=None, d_stats=None, scan_events=None, unroll: int = 0) -> SearchOpts:
+              d_chunk_at=None, d_stats=None, scan_events=None, unroll: int = 0,
+              flags: int = 0) -> SearchOpts:
     o = SearchOpts()
     o.d_seed = _ptr(d_seed)
     o.block_shift = block_shift
     o.threads = threads
     o.ht_slots = ht_slots
     o.unroll = unroll
+    o.flags = flags
     o.d_chunk_at = _ptr(d_chunk_at)
     o.d_stats = _ptr(d_stats)
     o._blocks = ctypes.c_uint32(0)

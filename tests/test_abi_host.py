@@ -56,8 +56,8 @@ def test_product_code_never_touches_the_oracle():
 
 
 def test_opts_struct_layout_matches_header():
-    # genie_search_opts: pointer, 4 x uint32, 2 pointers, host pointer, 2 events
+    # genie_search_opts: pointer, 4 x uint32, 2 pointers, host pointer, 2 events, flags (+pad)
     import ctypes
-    assert ctypes.sizeof(genie.SearchOpts) == 8 + 4 * 4 + 8 * 3 + 8 * 2
+    assert ctypes.sizeof(genie.SearchOpts) == 8 + 4 * 4 + 8 * 3 + 8 * 2 + 8
     assert ctypes.sizeof(genie.IndexInfo) == 40
     assert ctypes.sizeof(genie.QueriesInfo) == 24

@@ -111,13 +111,33 @@ def test_final_audit_threshold_is_kth_count_plus_one_per_range():
     qs = runner.compile_queries(idx, w)
     groups = (w.n_objects + (1 << shift) - 1) >> shift
     at = torch.zeros(w.n_queries * groups, dtype=torch.int32, device="cuda")
-    opts = genie.make_opts(block_shift=shift, d_chunk_at=at)
+    opts = genie.make_opts(block_shift=shift, d_chunk_at=at, flags=genie.GENIE_SEARCH_PER_RANGE_AT)
     runner.search(idx, qs, w.k, opts=opts)
     at = runner.u32(at).reshape(w.n_queries, groups)
     for g in range(groups):
         lo, hi = g << shift, min(w.n_objects, (g + 1) << shift)
         ref = oracle.topk(w, obj_range=(lo, hi))
         assert np.array_equal(at[:, g] - 1, ref["tk"]), g
+
+
+def test_shared_audit_threshold_starts_no_higher_than_the_kth_count():
+    """With the ranges of a query sharing their k-th counts, each range's
+    final AT is at least its own k-th count + 1 and at most the query's."""
+    w = synth.lsh(50_000, 12, 20, config=17)
+    shift = 13
+    idx = runner.build_index(w, 12)
+    qs = runner.compile_queries(idx, w)
+    groups = (w.n_objects + (1 << shift) - 1) >> shift
+    at = torch.zeros(w.n_queries * groups, dtype=torch.int32, device="cuda")
+    res = runner.search(idx, qs, w.k, opts=genie.make_opts(block_shift=shift, d_chunk_at=at)).host()
+    at = runner.u32(at).reshape(w.n_queries, groups)
+    full = oracle.topk(w)
+    assert_same(res, full)
+    for g in range(groups):
+        lo, hi = g << shift, min(w.n_objects, (g + 1) << shift)
+        local = oracle.topk(w, obj_range=(lo, hi))
+        assert np.all(at[:, g] - 1 >= local["tk"])
+        assert np.all(at[:, g] - 1 <= np.maximum(full["tk"], local["tk"]))
 
 
 def test_compiler_facts_match_the_oracle():
