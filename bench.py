@@ -299,6 +299,20 @@ def run_genie(args, rank, world, local):
     h2d = (Q + 1) * 4 + int(w.q_off[-1]) * 4
     d2h = 2 * Q * K * 4 + Q * 4
 
+    # the same batch with the Gate idle (count, then select from the counters):
+    # the on-chip form of the paper's GEN-SPQ comparison, timed after the run
+    ng_opts = genie.make_opts(flags=genie.GENIE_SEARCH_NO_GATE)
+
+    def step_no_gate():
+        qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
+        genie.genie_search(idx, qs, K, out.ids, out.counts, out.n_valid, opts=ng_opts,
+                           stream=stream)
+
+    step_no_gate()
+    ng_ms, _ = timed_steps(step_no_gate, max(3, args.steps // 3), stream)
+    ng_ms /= max(3, args.steps // 3)
+    cal = genie.genie_calibrate()
+
     # c-PQ counters from one more (untimed) pass
     stats = torch.zeros(8, dtype=torch.int64, device="cuda")
     qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
@@ -327,6 +341,13 @@ def run_genie(args, rank, world, local):
                      "frac": achieved / peak, "traffic": traffic_from_profile(src),
                      "kernel": "scan_cpq_kernel<4>", "peak_kind": peak_kind + " hbm_gbs",
                      "scan_ms": scan_ms, "algorithmic_bytes_per_launch": algo_bytes},
+        "smem_atomic_roofline": {
+            "bound": "shared-memory atomic adds (one per posting)",
+            "achieved": entries / (scan_ms / 1e3), "peak": cal.smem_atomics_per_s,
+            "unit": "updates/s", "frac": entries / (scan_ms / 1e3) / cal.smem_atomics_per_s,
+            "peak_kind": "measured by genie_calibrate on this GPU"},
+        "ablation_no_gate": {"ms_per_step": ng_ms, "value": Q * world / (ng_ms / 1e3),
+                             "c_pq_vs_no_gate": ng_ms / (total_ms / args.steps)},
         "e2e": {"value": Q * world * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 3 * args.steps,

@@ -165,7 +165,10 @@ genie_status genie_compile_ranges(const genie_index* index, uint32_t values_per_
                                   const int32_t* d_lo, const int32_t* d_hi, uint32_t n_queries,
                                   genie_stream stream, genie_queries** out);
 
-/* Release compiled queries (NULL is ignored).  Synchronises the device. */
+/* Release compiled queries (NULL is ignored).  The memory is freed in order
+ * on the stream the queries were compiled on (stream-ordered, no device-wide
+ * synchronisation): work on that stream that uses them completes first; work
+ * on other streams must be finished or ordered before it by the caller. */
 void genie_queries_destroy(genie_queries* queries);
 
 genie_status genie_queries_get_info(const genie_queries* queries, genie_queries_info* out);
@@ -227,6 +230,12 @@ typedef struct {
  * AuditThreshold of Theorem 3.1 in d_chunk_at. */
 #define GENIE_SEARCH_PER_RANGE_AT 1u
 
+/* Ablation: count every posting into the Bitmap Counter and select each
+ * range's top-k from the counters alone, with the Gate and hash table idle
+ * (the dense-count-then-select design the paper compares c-PQ with, GEN-SPQ
+ * of Sec. 6.1.2, with the counters on chip).  Same results. */
+#define GENIE_SEARCH_NO_GATE 2u
+
 /*
  * Top-k of every query.  By default the ranges of a query share what they
  * learn: a range starts its AuditThreshold at the largest k-th count of the
@@ -245,6 +254,24 @@ typedef struct {
 genie_status genie_search(const genie_index* index, const genie_queries* queries, uint32_t k,
                           const uint32_t* d_k, const genie_search_opts* opts, uint32_t* d_ids,
                           uint32_t* d_counts, uint32_t* d_n_valid, genie_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Device calibration                                                        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  double smem_atomics_per_s;  /* shared-memory atomic adds with return per second, whole GPU */
+  uint32_t sms;
+  double seconds;             /* duration of the timed launch */
+} genie_calibration;
+
+/*
+ * Measure the ceiling of the scan kernel's counter updates: one block per SM
+ * fills a 128 KB shared counter array and every thread issues atomic adds of
+ * 16-bit lane increments at pseudo-random words, using each returned value.
+ * Synchronises the device.  The paper has no counterpart.
+ */
+genie_status genie_calibrate(genie_calibration* out);
 
 /* ------------------------------------------------------------------------ */
 /* Batched search: one persistent, CUDA-graph-captured launch per batch      */

@@ -44,6 +44,9 @@ struct ScanArgs {
   // k-th largest of a subset never exceeds that of the whole set), so a range
   // may start its AuditThreshold there without losing any top-k object.
   uint32_t* at_hint;
+  // 1: count only, then select from the Bitmap Counter (the Gate and the
+  // hash table stay idle) -- the GEN-SPQ-style ablation of Sec. 6.1.2
+  uint32_t no_gate;
 };
 
 constexpr uint32_t kMaxProbe = 32;   // hash-table probes before an insert gives up
@@ -93,6 +96,20 @@ __device__ uint32_t collect_lanes(const uint32_t* bc, uint32_t nwords, uint32_t 
     }
   }
   return min(total, limit);
+}
+
+// Number of lanes whose count is at least `value` (all threads of the block).
+template <int LOG2W>
+__device__ uint32_t count_at_least(const uint32_t* bc, uint32_t nwords, uint32_t value,
+                                   uint32_t* scratch) {
+  constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, MASK = (1u << W) - 1u;
+  uint32_t m = 0;
+  for (uint32_t w = threadIdx.x; w < nwords; w += blockDim.x) {
+    const uint32_t word = bc[w];
+#pragma unroll
+    for (uint32_t l = 0; l < PER; ++l) m += ((word >> (l * W)) & MASK) >= value;
+  }
+  return dev::block_sum(m, scratch);
 }
 
 template <int LOG2W>
@@ -335,7 +352,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
       // Gate (Algorithm 1, lines 3-7): postings whose new count reaches the
       // (possibly stale) AuditThreshold join the warp's queue; the warp runs
       // the Gate on 32 queued candidates at a time.
-      const uint32_t at_c = vld(&s_at);
+      const uint32_t at_c = A.no_gate ? 0xFFFFFFFFu : vld(&s_at);
       uint32_t cm = 0;
 #pragma unroll
       for (uint32_t i = 0; i < 4 * kUnroll; ++i) cm |= (uint32_t)(val[i] >= at_c) << i;
@@ -399,7 +416,20 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   }
 
   // ---- finalise AT (Lemma 3.1) and read out this range's top-k ----------
-  if (tid == 0) {
+  const uint32_t nwords_local = (n_local + PER - 1) / PER;
+  if (A.no_gate) {
+    // the k-th count of the range: largest x with #{count >= x} >= k
+    uint32_t lo_x = 0, hi_x = B;
+    while (lo_x < hi_x) {
+      const uint32_t mid = (lo_x + hi_x + 1) >> 1;
+      if (count_at_least<LOG2W>(bc, nwords_local, mid, scratch) >= kq) lo_x = mid;
+      else hi_x = mid - 1;
+    }
+    if (tid == 0) {
+      s_at = lo_x + 1;
+      s_n = 0;
+    }
+  } else if (tid == 0) {
     uint32_t a = s_at;
     while (a <= B && za[a] >= kq) ++a;
     s_at = a;
@@ -407,7 +437,6 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   }
   __syncthreads();
   const uint32_t at_f = s_at;
-  const uint32_t nwords_local = (n_local + PER - 1) / PER;
   unsigned long long* out = A.cand + ((unsigned long long)qi * A.n_groups + g) * A.k;
   // Theorem 3.1: the objects with count >= AT_f are candidates in the HT; their
   // number is exactly ZA[AT_f] (every object at or above AT_f passed that level
@@ -424,7 +453,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   }
   __syncthreads();
   uint32_t n_hi = s_n;
-  const bool certified = !s_flags[0] && n_hi == want && n_hi < kq;
+  const bool certified = !A.no_gate && !s_flags[0] && n_hi == want && n_hi < kq;
   if (!certified)  // Bitmap-Counter selection of the same set
     n_hi = collect_lanes<LOG2W, true>(bc, nwords_local, at_f, kq, obj_base, cand, scratch);
   __syncthreads();

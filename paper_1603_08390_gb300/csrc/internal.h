@@ -65,6 +65,9 @@ struct genie_queries {
   uint32_t* bound = nullptr;     // [n_queries]
   uint64_t* entries = nullptr;   // [n_queries]
   float* features = nullptr;     // [n_queries * 64]
+  uint32_t* flags = nullptr;     // compile flags (64 bytes)
+  void* base = nullptr;          // the one stream-ordered allocation holding all of the above
+  cudaStream_t stream = nullptr; // the stream it was allocated (and is freed) on
 };
 
 namespace genie {

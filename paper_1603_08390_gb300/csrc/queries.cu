@@ -134,31 +134,37 @@ __global__ void range_expand_kernel(const uint32_t* __restrict__ item_off,
 
 void free_queries(genie_queries* q) {
   if (!q) return;
-  cudaFree(q->q_off);
-  cudaFree(q->q_kw);
-  cudaFree(q->bound);
-  cudaFree(q->entries);
-  cudaFree(q->features);
+  if (q->base) cudaFreeAsync(q->base, q->stream);
   delete q;
 }
 
+// One stream-ordered allocation holds every array of the handle, plus 64 bytes
+// of compile flags at the end.
 genie_status alloc_queries(const genie_index* index, uint32_t n_queries, uint64_t n_kw,
-                           genie_queries** out) {
+                           cudaStream_t s, genie_queries** out) {
   genie_queries* q = new (std::nothrow) genie_queries();
   if (!q) return fail(GENIE_ERR_OUT_OF_MEMORY, "query handle");
   q->index = index;
   cudaGetDevice(&q->device);
+  q->stream = s;
   q->n_queries = n_queries;
   q->n_keywords = n_kw;
-  cudaError_t e = cudaMalloc(&q->q_off, ((uint64_t)n_queries + 1) * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&q->q_kw, std::max<uint64_t>(n_kw, 1) * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&q->bound, (uint64_t)n_queries * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&q->entries, (uint64_t)n_queries * 8);
-  if (e == cudaSuccess) e = cudaMalloc(&q->features, (uint64_t)n_queries * kFeatures * 4);
+  auto up = [](uint64_t b) { return (b + 255) & ~(uint64_t)255; };
+  const uint64_t b_off = up(((uint64_t)n_queries + 1) * 4), b_kw = up(std::max<uint64_t>(n_kw, 1) * 4);
+  const uint64_t b_bound = up((uint64_t)n_queries * 4), b_ent = up((uint64_t)n_queries * 8);
+  const uint64_t b_feat = up((uint64_t)n_queries * kFeatures * 4);
+  cudaError_t e = cudaMallocAsync(&q->base, b_off + b_kw + b_bound + b_ent + b_feat + 256, s);
   if (e != cudaSuccess) {
-    free_queries(q);
-    return fail_cuda(e, "cudaMalloc(queries)");
+    delete q;
+    return fail_cuda(e, "cudaMallocAsync(queries)");
   }
+  char* p = static_cast<char*>(q->base);
+  q->q_off = reinterpret_cast<uint32_t*>(p);
+  q->q_kw = reinterpret_cast<uint32_t*>(p + b_off);
+  q->bound = reinterpret_cast<uint32_t*>(p + b_off + b_kw);
+  q->entries = reinterpret_cast<uint64_t*>(p + b_off + b_kw + b_bound);
+  q->features = reinterpret_cast<float*>(p + b_off + b_kw + b_bound + b_ent);
+  q->flags = reinterpret_cast<uint32_t*>(p + b_off + b_kw + b_bound + b_ent + b_feat);
   *out = q;
   return GENIE_OK;
 }
@@ -205,20 +211,16 @@ extern "C" genie_status genie_make_queries(const genie_index* index, const uint3
   const uint64_t n_kw = ends[1];
   if (n_kw > 0 && !d_q_kw) return fail(GENIE_ERR_INVALID_ARG, "genie_make_queries: d_q_kw is NULL");
   genie_queries* q = nullptr;
-  genie_status st = alloc_queries(index, n_queries, n_kw, &q);
+  genie_status st = alloc_queries(index, n_queries, n_kw, s, &q);
   if (st != GENIE_OK) return st;
-  uint32_t* flags = nullptr;
-  cudaError_t e = cudaMalloc(&flags, 64);
-  if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 64, s);
+  cudaError_t e = cudaMemsetAsync(q->flags, 0, 64, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(q->q_off, d_q_off, ((uint64_t)n_queries + 1) * 4, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess && n_kw) e = cudaMemcpyAsync(q->q_kw, d_q_kw, n_kw * 4, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) {
-    cudaFree(flags);
     free_queries(q);
     return fail_cuda(e, "genie_make_queries");
   }
-  st = finish(q, nullptr, flags, s, "genie_make_queries");
-  cudaFree(flags);
+  st = finish(q, nullptr, q->flags, s, "genie_make_queries");
   if (st != GENIE_OK) {
     free_queries(q);
     return st;
@@ -249,7 +251,7 @@ extern "C" genie_status genie_compile_ranges(const genie_index* index, uint32_t 
   const uint32_t n_dims = index->vocab / values_per_dim;
 
   uint32_t* buf = nullptr;  // flags[16] then counts/offsets[n_queries + 1]
-  GENIE_CUDA_TRY(cudaMalloc(&buf, 64 + ((uint64_t)n_queries + 1) * 4));
+  GENIE_CUDA_TRY(cudaMallocAsync((void**)&buf, 64 + ((uint64_t)n_queries + 1) * 4, s));
   uint32_t* flags = buf;
   uint32_t* cnt = buf + 16;
   cudaError_t e = cudaMemsetAsync(flags, 0, 64, s);
@@ -265,7 +267,7 @@ extern "C" genie_status genie_compile_ranges(const genie_index* index, uint32_t 
   if (e == cudaSuccess) e = cudaMemcpyAsync(&total, cnt + n_queries, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
-    cudaFree(buf);
+    cudaFreeAsync(buf, s);
     return fail_cuda(e, "genie_compile_ranges");
   }
   const char* bad = h[kBadOffsets] ? "item offsets are not non-decreasing"
@@ -273,29 +275,29 @@ extern "C" genie_status genie_compile_ranges(const genie_index* index, uint32_t 
                     : (h[kBadRange] & 1u) ? "an item has lo > hi"
                     : (h[kBadRange] & 2u) ? "a query expands to too many keywords" : nullptr;
   if (bad) {
-    cudaFree(buf);
+    cudaFreeAsync(buf, s);
     return fail(GENIE_ERR_INVALID_ARG, std::string("genie_compile_ranges: ") + bad);
   }
   genie_queries* q = nullptr;
-  genie_status st = alloc_queries(index, n_queries, total, &q);
+  genie_status st = alloc_queries(index, n_queries, total, s, &q);
   if (st != GENIE_OK) {
-    cudaFree(buf);
+    cudaFreeAsync(buf, s);
     return st;
   }
   e = cudaMemcpyAsync(q->q_off, cnt, ((uint64_t)n_queries + 1) * 4, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 64, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(q->flags, 0, 64, s);
   if (e == cudaSuccess) {
     range_expand_kernel<<<grid, 256, 0, s>>>(d_item_off, d_dim, d_lo, d_hi, n_queries,
                                              values_per_dim, q->q_off, q->q_kw);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {
-    cudaFree(buf);
+    cudaFreeAsync(buf, s);
     free_queries(q);
     return fail_cuda(e, "genie_compile_ranges");
   }
-  st = finish(q, d_item_off, flags, s, "genie_compile_ranges");
-  cudaFree(buf);
+  st = finish(q, d_item_off, q->flags, s, "genie_compile_ranges");
+  cudaFreeAsync(buf, s);
   if (st != GENIE_OK) {
     free_queries(q);
     return st;
@@ -306,8 +308,7 @@ extern "C" genie_status genie_compile_ranges(const genie_index* index, uint32_t 
 
 extern "C" void genie_queries_destroy(genie_queries* queries) {
   if (!queries) return;
-  cudaDeviceSynchronize();
-  free_queries(queries);
+  free_queries(queries);  // stream-ordered on the stream the queries were compiled on
 }
 
 extern "C" genie_status genie_queries_get_info(const genie_queries* queries, genie_queries_info* out) {

@@ -120,6 +120,7 @@ cudaError_t run_pass(const genie_index* idx, const genie_queries* qs, uint32_t k
   a.chunk_at = (o && !sel) ? o->d_chunk_at : nullptr;
   a.stats = o ? o->d_stats : nullptr;
   a.at_hint = at_hint;
+  a.no_gate = (o && (o->flags & GENIE_SEARCH_NO_GATE)) ? 1u : 0u;
   const bool timed = o && !sel && o->scan_event_begin && o->scan_event_end;
   if (timed) cudaEventRecord((cudaEvent_t)o->scan_event_begin, s);
   cudaError_t e = dispatch_scan(a, p, s);

@@ -25,6 +25,7 @@ GENIE_ERR_TIMEOUT = 5
 GENIE_MAX_K = 1024
 GENIE_MAX_BOUND = 4095
 GENIE_SEARCH_PER_RANGE_AT = 1
+GENIE_SEARCH_NO_GATE = 2
 N_FEATURES = 64
 
 EXPORTED = (
@@ -36,7 +37,7 @@ EXPORTED = (
     "genie_mlp_adam_step", "genie_mlp_train", "genie_mlp_seeds", "genie_autotune",
     "genie_batch_create", "genie_batch_get_info", "genie_batch_destroy", "genie_batch_run",
     "genie_server_clock", "genie_server_create", "genie_server_destroy", "genie_server_submit",
-    "genie_server_poll", "genie_server_get_stats", "genie_server_replay",
+    "genie_server_poll", "genie_server_get_stats", "genie_server_replay", "genie_calibrate",
 )
 
 
@@ -82,6 +83,11 @@ class ServerStats(ctypes.Structure):
                 ("deferred_admissions", ctypes.c_uint64),
                 ("max_queries_in_flight", ctypes.c_uint64), ("pending", ctypes.c_uint64),
                 ("reserved_bytes", ctypes.c_uint64)]
+
+
+class Calibration(ctypes.Structure):
+    _fields_ = [("smem_atomics_per_s", ctypes.c_double), ("sms", ctypes.c_uint32),
+                ("seconds", ctypes.c_double)]
 
 
 class SearchOpts(ctypes.Structure):
@@ -155,6 +161,8 @@ def load(path: Optional[str] = None):
         lib.genie_batch_destroy.argtypes = [vp]
         lib.genie_batch_destroy.restype = None
         lib.genie_batch_run.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        lib.genie_calibrate.argtypes = [ctypes.POINTER(Calibration)]
+        lib.genie_calibrate.restype = st
         lib.genie_server_clock.restype = ctypes.c_double
         lib.genie_server_clock.argtypes = []
         lib.genie_server_create.argtypes = [vp, ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
@@ -494,3 +502,10 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def genie_calibrate() -> Calibration:
+    lib = load()
+    out = Calibration()
+    _check(lib.genie_calibrate(ctypes.byref(out)), lib)
+    return out

@@ -356,3 +356,23 @@ def test_full_serving_index_8m_per_query_k_sampled():
     assert qs.max_bound <= 64  # 8-bit counters
     rows, ref = _sampled(w, 12, 3)
     assert_same(res, ref, rows)
+
+
+@pytest.mark.parametrize("maker", [lambda: synth.lsh(60_000, 32, 100, config=34),
+                                   lambda: synth.sets(150_000, (16, 256), 1 << 16, 48, (8, 512), 10,
+                                                      config=35),
+                                   lambda: synth.relational(n_objects=40_000, n_queries=32,
+                                                            config=36)])
+def test_gateless_ablation_selects_the_same_topk(maker):
+    """Counting first and selecting from the Bitmap Counter alone (the
+    GEN-SPQ-style ablation) gives exactly the c-PQ results."""
+    w = maker()
+    res, _, _ = run(w, chunk_shift=13, opts=genie.make_opts(block_shift=14,
+                                                             flags=genie.GENIE_SEARCH_NO_GATE))
+    assert_same(res, oracle.topk(w))
+
+
+def test_calibration_measures_a_positive_atomic_rate():
+    cal = genie.genie_calibrate()
+    assert cal.sms >= 1 and cal.seconds > 0
+    assert 1e9 < cal.smem_atomics_per_s < 1e14
