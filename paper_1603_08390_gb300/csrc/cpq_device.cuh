@@ -307,16 +307,37 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     // fewer); a warp's tile numbers only grow, so its segment cursor j only
     // moves forward
     uint32_t j = 0;
-    for (uint32_t t = warp; t < total_tiles;) {
-      while (tile_pre[j + 1] <= t) ++j;
-      const uint32_t lo = seg_lo[j], hi = seg_hi[j];
-      const uint32_t start = (lo & ~3u) + (t - tile_pre[j]) * kTile;
-      uint4 v[kUnroll];
+    // Locate tile tt (segment, bounds) and load its postings.  With two loads
+    // per lane the next tile is loaded while this one is counted (more
+    // registers would spill with four).
+    auto locate_load = [&](uint32_t tt, uint32_t& lo_, uint32_t& hi_, uint32_t& st_,
+                           uint4 (&vv)[U]) {
+      while (tile_pre[j + 1] <= tt) ++j;
+      lo_ = seg_lo[j];
+      hi_ = seg_hi[j];
+      st_ = (lo_ & ~3u) + (tt - tile_pre[j]) * kTile;
 #pragma unroll
       for (uint32_t u = 0; u < kUnroll; ++u) {
-        const uint32_t idx = start + (u * 32 + lane) * 4;
-        v[u] = idx < hi ? __ldg(reinterpret_cast<const uint4*>(A.post_ids + idx))
-                        : make_uint4(0, 0, 0, 0);
+        const uint32_t idx = st_ + (u * 32 + lane) * 4;
+        vv[u] = idx < hi_ ? __ldg(reinterpret_cast<const uint4*>(A.post_ids + idx))
+                          : make_uint4(0, 0, 0, 0);
+      }
+    };
+    constexpr bool kPrefetch = U == 2;
+    uint32_t t = warp, lo = 0, hi = 0, start = 0;
+    uint4 v[kUnroll];
+    if (kPrefetch && t < total_tiles) locate_load(t, lo, hi, start, v);
+    while (t < total_tiles) {
+      uint32_t nt = 0, lo1 = 0, hi1 = 0, start1 = 0;
+      uint4 v1[kUnroll];
+      if (kPrefetch) {
+        if (lane == 0) nt = atomicAdd(&s_next, 1u);
+        nt = __shfl_sync(0xFFFFFFFFu, nt, 0);
+#pragma unroll
+        for (uint32_t u = 0; u < kUnroll; ++u) v1[u] = make_uint4(0, 0, 0, 0);
+        if (nt < total_tiles) locate_load(nt, lo1, hi1, start1, v1);
+      } else {
+        locate_load(t, lo, hi, start, v);
       }
       // Bitmap Counter: one sub-word atomic add per posting (Algorithm 1,
       // lines 1-2); val = the object's new count, 0 for slots outside the list
@@ -402,9 +423,17 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
           }
         }
       }
-      uint32_t nt = 0;
-      if (lane == 0) nt = atomicAdd(&s_next, 1u);
-      t = __shfl_sync(0xFFFFFFFFu, nt, 0);
+      if (kPrefetch) {
+        t = nt;
+        lo = lo1;
+        hi = hi1;
+        start = start1;
+#pragma unroll
+        for (uint32_t u = 0; u < kUnroll; ++u) v[u] = v1[u];
+      } else {
+        if (lane == 0) nt = atomicAdd(&s_next, 1u);
+        t = __shfl_sync(0xFFFFFFFFu, nt, 0);
+      }
     }
     while (qn) {
       const uint32_t f = min(qn, 32u);
