@@ -51,18 +51,69 @@ struct ScanArgs {
 
 constexpr uint32_t kMaxProbe = 32;   // hash-table probes before an insert gives up
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
-constexpr uint32_t kMaxWarps = 32;   // per-warp Gate queues
-constexpr uint32_t kRing = 64;       // Gate candidates a warp can hold (power of two)
+constexpr uint32_t kTilePrePad = 4;  // tile prefix sums: the sentinel after the last keyword
+constexpr uint32_t kRun = 4;         // consecutive tiles a warp takes per claim
 
 size_t scan_smem_bytes(uint32_t log2w, uint32_t block_shift, uint32_t ht_slots, uint32_t za_len,
                        uint32_t k) {
   size_t words = ((size_t)1 << block_shift) >> (5 - log2w);
   size_t present = ((size_t)1 << block_shift) >> 5;
   return words * 4 + present * 4 + (size_t)ht_slots * 4 + (size_t)dev::next_pow2(k) * 8 +
-         (size_t)za_len * 4 + (3 * kKwBatch + 4) * 4 + (size_t)kMaxWarps * kRing * 2 * 4;
+         (size_t)za_len * 4 + (3 * kKwBatch + kTilePrePad) * 4;
 }
 
 __device__ __forceinline__ uint32_t vld(const uint32_t* p) { return *(const volatile uint32_t*)p; }
+
+// Counter lanes addressed by the object id itself.  A range starts at a
+// multiple of the lanes per word, so the word of object id is
+// byte_off(id) - byte_off(range start) bytes into the range's counters, and
+// the lane inside the word is the low bits of the id.  inc: the word-sized
+// increment of that lane; get: the lane's value in a counter word.
+template <int LOG2W>
+struct Lane;
+template <>
+struct Lane<4> {  // 16-bit counters, two per word
+  static __device__ __forceinline__ uint32_t byte_off(uint32_t id) { return (id & ~1u) << 1; }
+  static __device__ __forceinline__ uint32_t inc(uint32_t id) { return (id & 1u) * 0xFFFFu + 1u; }
+  static __device__ __forceinline__ uint32_t get(uint32_t w, uint32_t id) {
+    return __byte_perm(w, 0u, 0x4410u + (id & 1u) * 0x22u);  // bytes 2l, 2l+1, then zeros
+  }
+};
+template <>
+struct Lane<3> {  // 8-bit counters, four per word
+  static __device__ __forceinline__ uint32_t byte_off(uint32_t id) { return id & ~3u; }
+  static __device__ __forceinline__ uint32_t inc(uint32_t id) { return 1u << ((id & 3u) << 3); }
+  static __device__ __forceinline__ uint32_t get(uint32_t w, uint32_t id) {
+    return __byte_perm(w, 0u, 0x4440u | (id & 3u));  // byte l, then zeros
+  }
+};
+template <>
+struct Lane<2> {  // 4-bit counters, eight per word
+  static __device__ __forceinline__ uint32_t byte_off(uint32_t id) { return (id >> 1) & ~3u; }
+  static __device__ __forceinline__ uint32_t inc(uint32_t id) { return 1u << ((id & 7u) << 2); }
+  static __device__ __forceinline__ uint32_t get(uint32_t w, uint32_t id) {
+    return (w >> ((id & 7u) << 2)) & 0xFu;
+  }
+};
+
+// atomicAdd on a 32-bit shared-memory address, returning the old word
+__device__ __forceinline__ uint32_t atom_add_shared(uint32_t saddr, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(saddr), "r"(v) : "memory");
+  return old;
+}
+
+// The same, done only where p != 0 (predicated; the address is not touched
+// otherwise); returns 0 where p == 0.
+__device__ __forceinline__ uint32_t atom_add_shared_if(uint32_t p, uint32_t saddr, uint32_t v) {
+  uint32_t old = 0;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q atom.shared.add.u32 %0, [%1], %2;\n\t}"
+      : "+r"(old)
+      : "r"(saddr), "r"(v), "r"(p)
+      : "memory");
+  return old;
+}
 
 // First `limit` lanes (ascending id) whose count equals `value` (or is at
 // least `value` when AT_LEAST) become result keys dst[0..); returns how many.
@@ -155,49 +206,43 @@ __device__ __noinline__ void ht_insert(const GateState g, uint32_t id, uint32_t 
   g.flags[0] = 1;  // not placed: the read-out falls back to the Bitmap Counter
 }
 
-// The Gate of Algorithm 1 for n <= 32 candidates queued by one warp (lane l
-// takes entry head + l of the warp's ring).  Passes at the same level share one ZipperArray atomic;
-// z numbers a pass within its level; the first k passes of a level are
-// hash-table candidates; a full level advances AT.  Returns the passes of
-// this lane (0/1) and adds its inserts to *n_ins.
+// AT advance of Algorithm 1 (lines 5-6): while ZA[AT] >= k, AT grows by one.
+// AT is read without locking and raised by atomicMax, so concurrent callers
+// only ever move it up to a level whose ZipperArray entry has reached k.
+__device__ __noinline__ void advance_at(const GateState g, uint32_t kq, uint32_t B) {
+  uint32_t a = vld(g.at);
+  while (a <= B && vld(&g.za[a]) >= kq) {
+    atomicMax(g.at, a + 1);
+    ++a;
+  }
+}
+
+// The Gate of Algorithm 1 (lines 3-7) for one posting that made object id's
+// count c >= AT: the pass is numbered z at its level by the ZipperArray
+// increment; the first k passes of a level are hash-table candidates (each
+// object inserted once while it holds its presence bit); the pass that fills
+// a level to k advances AT.  AT may lag behind a full level for a while (a
+// stale AT only admits more passes); the read-out recomputes AT_f.
 template <int LOG2W>
-__device__ __noinline__ uint32_t gate_flush(const GateState g, const uint32_t* ring, uint32_t head,
-                                            uint32_t n, uint32_t kq, uint32_t B, uint32_t obj_base,
-                                            uint32_t ht_mask, uint32_t ht_bits, uint32_t* n_ins) {
-  const uint32_t lane = dev::lane_id();
-  __syncwarp();
-  const bool act = lane < n;
-  const uint32_t slot = (head + lane) & (kRing - 1);
-  const uint32_t id = act ? ring[slot] : 0u;
-  const uint32_t val = act ? ring[kRing + slot] : 0u;
-  __syncwarp();
-  if (act && val > B) g.flags[1] = 1;  // cannot happen with a valid bound
-  const bool pass = act && val >= vld(g.at) && val <= B;
-  const uint32_t m = __ballot_sync(0xFFFFFFFFu, pass);
-  if (!pass) return 0;
-  const uint32_t peers = __match_any_sync(m, val);
-  const uint32_t leader = __ffs(peers) - 1, n_peers = __popc(peers);
-  const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(&g.za[val], n_peers);
-  base = __shfl_sync(peers, base, leader);
-  const uint32_t z = base + rank;
+__device__ __forceinline__ void gate_pass(const GateState& g, uint32_t id, uint32_t c,
+                                          uint32_t kq, uint32_t B, uint32_t obj_base,
+                                          uint32_t ht_mask, uint32_t ht_bits, uint32_t& n_gate,
+                                          uint32_t& n_ins) {
+  if (c > B) {  // cannot happen with a valid bound
+    g.flags[1] = 1;
+    return;
+  }
+  const uint32_t z = atomicAdd(&g.za[c], 1u);
+  ++n_gate;
   if (z < kq) {
     const uint32_t local = id - obj_base;
     const uint32_t w = local >> 5, b = 1u << (local & 31);
     if (!(vld(&g.present[w]) & b) && !(atomicOr(&g.present[w], b) & b)) {
-      ++*n_ins;
+      ++n_ins;
       ht_insert<LOG2W>(g, id, obj_base, ht_mask, ht_bits);
     }
   }
-  if (rank == n_peers - 1 && z + 1 >= kq) {  // level full: advance AT
-    uint32_t a = vld(g.at);
-    while (a <= B && vld(&g.za[a]) >= kq) {
-      atomicMax(g.at, a + 1);
-      ++a;
-    }
-  }
-  return 1;
+  if (z + 1 == kq) advance_at(g, kq, B);
 }
 
 // LOG2W: log2 of the counter width; U: 16-byte loads in flight per lane (a
@@ -222,7 +267,7 @@ struct BlockShared {
 template <int LOG2W, int U>
 __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_t g,
                                          uint4* smem_raw, BlockShared& S) {
-  constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, LPW = 5 - LOG2W, MASK = (1u << W) - 1u;
+  constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, LPW = 5 - LOG2W;
   constexpr uint32_t kUnroll = U, kTile = 32 * 4 * U;
   uint32_t& s_at = S.at;
   uint32_t& s_n = S.n;
@@ -240,11 +285,9 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   uint32_t* present = bc + nwords;
   uint32_t* ht = present + npresent;
   unsigned long long* cand = reinterpret_cast<unsigned long long*>(ht + A.ht_slots);
-  uint32_t* za = reinterpret_cast<uint32_t*>(cand + kpad);
-  uint32_t* seg_lo = za + A.za_len;
-  uint32_t* seg_hi = seg_lo + kKwBatch;
-  uint32_t* tile_pre = seg_hi + kKwBatch;
-  uint32_t* gq = tile_pre + kKwBatch + 4;  // [warp][id x kRing | val x kRing]
+  uint2* seg = reinterpret_cast<uint2*>(cand + kpad);  // [keyword] (lo, hi) in the List Array
+  uint32_t* za = reinterpret_cast<uint32_t*>(seg + kKwBatch);
+  uint32_t* tile_pre = za + A.za_len;  // [keyword] first tile, then the tile count
 
   const uint32_t tid = threadIdx.x, lane = dev::lane_id(), warp = dev::warp_id();
   const uint32_t nwarps = blockDim.x >> 5;
@@ -275,13 +318,14 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
 
   uint32_t n_gate = 0, n_ins = 0;
 
-  uint32_t* ring = gq + warp * 2 * kRing;  // this warp's Gate queue
-  uint32_t qh = 0, qn = 0;                 // head and length
   const GateState gs{za, present, ht, bc, &s_at, s_flags};
 
   // ---- scan: all postings of the query's keywords inside this id range ---
   const uint32_t qa = A.q_off[q], qb = A.q_off[q + 1];
   const uint32_t stride = A.n_chunks + 1;
+  // shared address of the counter word of object id: bc_adj + byte_off(id)
+  const uint32_t bc_adj =
+      (uint32_t)__cvta_generic_to_shared(bc) - Lane<LOG2W>::byte_off(obj_base);
   for (uint32_t kb = qa; kb < qb; kb += kKwBatch) {
     const uint32_t nk = min(kKwBatch, qb - kb);
     uint32_t ntiles = 0;
@@ -290,31 +334,26 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
       const uint64_t base = A.kw_off[kw];
       const uint32_t* row = A.chunk_pos + (uint64_t)kw * stride;
       const uint32_t lo = (uint32_t)(base + row[c0]), hi = (uint32_t)(base + row[c1]);
-      seg_lo[tid] = lo;
-      seg_hi[tid] = hi;
+      seg[tid] = make_uint2(lo, hi);
       ntiles = hi > lo ? (hi - (lo & ~3u) + kTile - 1) / kTile : 0;
     }
     uint32_t total_tiles;
     uint32_t pre = dev::block_exclusive_scan(ntiles, scratch, &total_tiles);
     if (tid < nk) tile_pre[tid] = pre;
-    if (tid == 0) {
-      tile_pre[nk] = total_tiles;  // sentinel for the segment cursor
-      s_next = nwarps;
-    }
+    if (tid == 0) tile_pre[nk] = total_tiles;  // sentinel for the segment cursor
+    if (tid == 0) s_next = 2 * nwarps;
     __syncthreads();
 
-    // tiles are handed out dynamically (warps slowed by Gate work take
-    // fewer); a warp's tile numbers only grow, so its segment cursor j only
-    // moves forward
+    // Warps take runs of kRun consecutive tiles from a shared counter (warps
+    // slowed by Gate work take fewer runs); a warp's tile numbers only grow,
+    // so its segment cursor j only moves forward.
     uint32_t j = 0;
-    // Locate tile tt (segment, bounds) and load its postings.  With two loads
-    // per lane the next tile is loaded while this one is counted (more
-    // registers would spill with four).
     auto locate_load = [&](uint32_t tt, uint32_t& lo_, uint32_t& hi_, uint32_t& st_,
                            uint4 (&vv)[U]) {
       while (tile_pre[j + 1] <= tt) ++j;
-      lo_ = seg_lo[j];
-      hi_ = seg_hi[j];
+      const uint2 sg = seg[j];
+      lo_ = sg.x;
+      hi_ = sg.y;
       st_ = (lo_ & ~3u) + (tt - tile_pre[j]) * kTile;
 #pragma unroll
       for (uint32_t u = 0; u < kUnroll; ++u) {
@@ -323,123 +362,99 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
                           : make_uint4(0, 0, 0, 0);
       }
     };
+    // With two loads per lane the next tile is located and loaded while this
+    // one's counter updates are in flight (more registers would spill with
+    // four); the next run is claimed one run ahead.
     constexpr bool kPrefetch = U == 2;
-    uint32_t t = warp, lo = 0, hi = 0, start = 0;
+    uint32_t t = warp * kRun, t_end = min(t + kRun, total_tiles);
+    uint32_t pending = nwarps + warp;  // the run after the current one
+    uint32_t lo = 0, hi = 0, start = 0;
     uint4 v[kUnroll];
     if (kPrefetch && t < total_tiles) locate_load(t, lo, hi, start, v);
     while (t < total_tiles) {
-      uint32_t nt = 0, lo1 = 0, hi1 = 0, start1 = 0;
+      // the tile after t: the next of this run, else the first of the pending run
+      const bool run_ends = t + 1 >= t_end;
+      const uint32_t tn = run_ends ? pending * kRun : t + 1;
+      const uint32_t tn_end = run_ends ? min(tn + kRun, total_tiles) : t_end;
+      uint32_t claim = 0, lo1 = 0, hi1 = 0, start1 = 0;
       uint4 v1[kUnroll];
-      if (kPrefetch) {
-        if (lane == 0) nt = atomicAdd(&s_next, 1u);
-        nt = __shfl_sync(0xFFFFFFFFu, nt, 0);
+      if (!kPrefetch) locate_load(t, lo, hi, start, v);
+      // slots inside the list: four bits per 16-byte vector
+      uint32_t okm = 0xFFFFFFFFu;
+      if (start < lo || start + kTile > hi) {
+        okm = 0;
 #pragma unroll
-        for (uint32_t u = 0; u < kUnroll; ++u) v1[u] = make_uint4(0, 0, 0, 0);
-        if (nt < total_tiles) locate_load(nt, lo1, hi1, start1, v1);
-      } else {
-        locate_load(t, lo, hi, start, v);
+        for (uint32_t u = 0; u < kUnroll; ++u) {
+          const int p = (int)(start + (u * 32 + lane) * 4 - lo);  // >= -3
+          const int hc = min(max((int)(hi - lo) - p, 0), 4);
+          okm |= ((0xFu >> (4 - hc)) & (0xFu << (p < 0 ? -p : 0))) << (4 * u);
+        }
       }
       // Bitmap Counter: one sub-word atomic add per posting (Algorithm 1,
-      // lines 1-2); val = the object's new count, 0 for slots outside the list
+      // lines 1-2); val = the object's count before the add (0 for slots
+      // outside the list).  Every id of a sublist lies in this block's range.
       uint32_t val[4 * kUnroll];
-      if (start >= lo && start + kTile <= hi) {  // tile inside the list: no checks
-        // the index keeps every id of this range's sublists inside the range
+      if (okm == 0xFFFFFFFFu) {
 #pragma unroll
         for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
           const uint32_t u = i >> 2, e = i & 3;
           const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-          const uint32_t local = id - obj_base;
-          const uint32_t sh = (local & (PER - 1)) << LOG2W;
-          val[i] = ((atomicAdd(&bc[local >> LPW], 1u << sh) >> sh) & MASK) + 1u;
+          val[i] = atom_add_shared(bc_adj + Lane<LOG2W>::byte_off(id), Lane<LOG2W>::inc(id));
         }
       } else {
 #pragma unroll
         for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
           const uint32_t u = i >> 2, e = i & 3;
-          const uint32_t pos = start + (u * 32 + lane) * 4 + e;
           const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-          const uint32_t local = id - obj_base;
-          val[i] = 0;
-          if (pos >= lo && pos < hi) {
-            if (local < n_local) {
-              const uint32_t sh = (local & (PER - 1)) << LOG2W;
-              val[i] = ((atomicAdd(&bc[local >> LPW], 1u << sh) >> sh) & MASK) + 1u;
-            } else {
-              s_flags[1] = 1;  // an id outside this block's range: the index is inconsistent
-            }
-          }
+          val[i] = atom_add_shared_if(okm & (1u << i), bc_adj + Lane<LOG2W>::byte_off(id),
+                                      Lane<LOG2W>::inc(id));
         }
       }
-      // Gate (Algorithm 1, lines 3-7): postings whose new count reaches the
-      // (possibly stale) AuditThreshold join the warp's queue; the warp runs
-      // the Gate on 32 queued candidates at a time.
-      const uint32_t at_c = A.no_gate ? 0xFFFFFFFFu : vld(&s_at);
-      uint32_t cm = 0;
-#pragma unroll
-      for (uint32_t i = 0; i < 4 * kUnroll; ++i) cm |= (uint32_t)(val[i] >= at_c) << i;
-      if (__any_sync(0xFFFFFFFFu, cm)) {
-        const uint32_t nc = __popc(cm);
-        const uint32_t incl = dev::warp_inclusive_scan(nc);
-        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        if (qn + total > kRing) {  // make room: run the Gate on the backlog
-          while (qn) {
-            const uint32_t f = min(qn, 32u);
-            n_gate += gate_flush<LOG2W>(gs, ring, qh, f, kq, B, obj_base, ht_mask, ht_bits, &n_ins);
-            qh += f;
-            qn -= f;
-          }
-        }
-        if (total <= kRing) {
-          uint32_t p = qh + qn + incl - nc;
-#pragma unroll
-          for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
-            if ((cm >> i) & 1u) {
-              const uint32_t u = i >> 2, e = i & 3;
-              ring[p & (kRing - 1)] = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-              ring[kRing + (p & (kRing - 1))] = val[i];
-              ++p;
-            }
-          }
-          qn += total;
-          while (qn >= 32) {
-            n_gate += gate_flush<LOG2W>(gs, ring, qh, 32, kq, B, obj_base, ht_mask, ht_bits, &n_ins);
-            qh += 32;
-            qn -= 32;
-          }
-        } else {  // a burst larger than the queue: one element slot at a time
-#pragma unroll
-          for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
-            const bool c = (cm >> i) & 1u;
-            const uint32_t m = __ballot_sync(0xFFFFFFFFu, c);
-            if (m == 0) continue;
-            if (c) {
-              const uint32_t u = i >> 2, e = i & 3;
-              const uint32_t p = (qh + __popc(m & ((1u << lane) - 1u))) & (kRing - 1);
-              ring[p] = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-              ring[kRing + p] = val[i];
-            }
-            n_gate += gate_flush<LOG2W>(gs, ring, qh, __popc(m), kq, B, obj_base, ht_mask, ht_bits,
-                                        &n_ins);
-          }
-        }
-      }
+      if (run_ends && lane == 0) claim = atomicAdd(&s_next, 1u);  // the run after pending
       if (kPrefetch) {
-        t = nt;
+#pragma unroll
+        for (uint32_t u = 0; u < kUnroll; ++u) v1[u] = make_uint4(0, 0, 0, 0);
+        if (tn < total_tiles) locate_load(tn, lo1, hi1, start1, v1);
+      }
+      uint32_t vmax = 0;
+#pragma unroll
+      for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
+        const uint32_t u = i >> 2, e = i & 3;
+        const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
+        val[i] = Lane<LOG2W>::get(val[i], id);
+        vmax = max(vmax, val[i]);
+      }
+      // Gate (Algorithm 1, lines 3-7) for the postings whose new count val + 1
+      // reaches the (possibly stale) AuditThreshold: rare, so a tile is tested
+      // once on each lane's largest count.
+      const uint32_t at_c = A.no_gate ? 0xFFFFFFFFu : vld(&s_at);
+      if (__any_sync(0xFFFFFFFFu, vmax + 1 >= at_c)) {
+        uint32_t pm = 0;  // this lane's passing slots
+#pragma unroll
+        for (uint32_t i = 0; i < 4 * kUnroll; ++i) pm |= (uint32_t)(val[i] + 1 >= at_c) << i;
+        pm &= okm;
+        const uint32_t wm = __reduce_or_sync(0xFFFFFFFFu, pm);
+#pragma unroll
+        for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
+          if ((wm >> i) & 1u) {  // some lane passes at slot i
+            const uint32_t u = i >> 2, e = i & 3;
+            const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
+            if ((pm >> i) & 1u)
+              gate_pass<LOG2W>(gs, id, val[i] + 1, kq, B, obj_base, ht_mask, ht_bits, n_gate,
+                               n_ins);
+          }
+        }
+      }
+      if (run_ends) pending = __shfl_sync(0xFFFFFFFFu, claim, 0);
+      t = tn;
+      t_end = tn_end;
+      if (kPrefetch) {
         lo = lo1;
         hi = hi1;
         start = start1;
 #pragma unroll
         for (uint32_t u = 0; u < kUnroll; ++u) v[u] = v1[u];
-      } else {
-        if (lane == 0) nt = atomicAdd(&s_next, 1u);
-        t = __shfl_sync(0xFFFFFFFFu, nt, 0);
       }
-    }
-    while (qn) {
-      const uint32_t f = min(qn, 32u);
-      n_gate += gate_flush<LOG2W>(gs, ring, qh, f, kq, B, obj_base, ht_mask, ht_bits, &n_ins);
-      qh += f;
-      qn -= f;
     }
     __syncthreads();
   }
