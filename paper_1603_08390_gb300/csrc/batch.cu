@@ -156,7 +156,8 @@ struct genie_batch {
   genie::BatchDesc* desc = nullptr;
   unsigned long long* cand = nullptr;
   uint32_t* order = nullptr;
-  uint32_t* counters = nullptr;  // [0] work, [1 ..] done, then [max_queries] shared k-th counts
+  uint32_t* counters = nullptr;  // [0] work, [1 ..] done, [max_queries] seeds, histograms
+  uint64_t counter_words = 0;
   cudaStream_t capture_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -234,7 +235,12 @@ extern "C" genie_status genie_batch_create(const genie_index* index, uint32_t ma
   cudaError_t e = cudaMalloc(&b->desc, sizeof(BatchDesc));
   if (e == cudaSuccess) e = cudaMalloc(&b->cand, (uint64_t)max_queries * p.n_groups * k * 8);
   if (e == cudaSuccess) e = cudaMalloc(&b->order, (uint64_t)max_queries * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&b->counters, (2 * (uint64_t)max_queries + 1) * 4);
+  // work counter, per-query done counts and seeds, then per-query count
+  // histograms of the finished ranges (when they stay small)
+  const uint64_t hist_words = (uint64_t)max_queries * p.za_len;
+  const bool use_hist = hist_words * 4 <= kHintHistMaxBytes;
+  b->counter_words = 2 * (uint64_t)max_queries + 1 + (use_hist ? hist_words : 0);
+  if (e == cudaSuccess) e = cudaMalloc(&b->counters, b->counter_words * 4);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     free_batch(b);
@@ -257,6 +263,8 @@ extern "C" genie_status genie_batch_create(const genie_index* index, uint32_t ma
   d.scan.za_len = p.za_len;
   d.scan.cand = b->cand;
   d.scan.at_hint = b->counters + 1 + max_queries;
+  d.scan.hint_hist = use_hist ? b->counters + 1 + 2 * (uint64_t)max_queries : nullptr;
+  d.scan.hint_stride = p.za_len;
   d.merge.cand = b->cand;
   d.merge.n_groups = p.n_groups;
   d.merge.k = k;
@@ -271,7 +279,7 @@ extern "C" genie_status genie_batch_create(const genie_index* index, uint32_t ma
   if (e == cudaSuccess) e = batch_dispatch(b, false);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaMemsetAsync(b->counters, 0, (2 * (uint64_t)max_queries + 1) * 4, cs);
+    cudaMemsetAsync(b->counters, 0, b->counter_words * 4, cs);
     order_kernel<<<1, 1024, osmem, cs>>>(b->desc);
     cudaError_t le = batch_dispatch(b, true);
     e = cudaStreamEndCapture(cs, &b->graph);

@@ -44,6 +44,12 @@ struct ScanArgs {
   // k-th largest of a subset never exceeds that of the whole set), so a range
   // may start its AuditThreshold there without losing any top-k object.
   uint32_t* at_hint;
+  // [n_sel][hint_stride] or NULL: per query, how many objects its finished
+  // ranges reported at each count.  They are distinct objects with exact
+  // counts, so the k-th largest count among them is also at most the query's
+  // k-th count; it replaces the single largest range k-th count in at_hint.
+  uint32_t* hint_hist;
+  uint32_t hint_stride;
   // 1: count only, then select from the Bitmap Counter (the Gate and the
   // hash table stay idle) -- the GEN-SPQ-style ablation of Sec. 6.1.2
   uint32_t no_gate;
@@ -245,6 +251,46 @@ __device__ __forceinline__ void gate_pass(const GateState& g, uint32_t id, uint3
   if (z + 1 == kq) advance_at(g, kq, B);
 }
 
+// Largest x in 1..B with h[x] + ... + h[B] >= k (0 if there is none): the
+// k-th largest count of the objects the histogram h counts.  h is read
+// through L2 (other blocks add to it).  All threads of the block call it.
+__device__ __forceinline__ uint32_t hist_kth(const uint32_t* h, uint32_t B, uint32_t k,
+                                             uint32_t* scratch, uint32_t& s_res) {
+  if (threadIdx.x == 0) s_res = 0;
+  uint32_t carry = 0;
+  for (uint32_t top = B; top >= 1;) {  // levels top, top - 1, ... from the highest
+    const uint32_t n = min(top, blockDim.x);
+    const uint32_t c = threadIdx.x < n ? top - threadIdx.x : 0u;
+    const uint32_t v = c ? __ldcg(&h[c]) : 0u;
+    uint32_t total;
+    const uint32_t incl = carry + dev::block_exclusive_scan(v, scratch, &total) + v;
+    if (c && incl >= k && incl - v < k) s_res = c;  // the level where the sum reaches k
+    __syncthreads();
+    const uint32_t r = s_res;
+    if (r || carry + total >= k) return r;
+    carry += total;
+    top -= n;
+  }
+  return 0;
+}
+
+// Adds a finished range's reported counts (cand[0..n_hi) and n_tie ties at
+// at_f - 1) to its query's histogram hh, then raises the query's seed to the
+// k-th largest count of everything its finished ranges reported.  All
+// threads of the block call it.
+__device__ __noinline__ void publish_seed(uint32_t* hh, uint32_t* seed,
+                                          const unsigned long long* cand, uint32_t n_hi,
+                                          uint32_t n_tie, uint32_t at_f, uint32_t B, uint32_t k,
+                                          uint32_t* scratch, uint32_t* s_res) {
+  for (uint32_t i = threadIdx.x; i < n_hi; i += blockDim.x)
+    atomicAdd(&hh[dev::key_count(cand[i])], 1u);
+  if (threadIdx.x == 0 && n_tie) atomicAdd(&hh[at_f - 1], n_tie);
+  __threadfence();
+  __syncthreads();
+  const uint32_t x = hist_kth(hh, B, k, scratch, *s_res);
+  if (threadIdx.x == 0 && x) atomicMax(seed, x);
+}
+
 // LOG2W: log2 of the counter width; U: 16-byte loads in flight per lane (a
 // warp tile is 128 * U postings); THREADS: block size.
 // Static shared state of one block.
@@ -254,6 +300,7 @@ struct BlockShared {
   uint32_t next;      // next tile of the current keyword batch
   uint32_t item;      // persistent blocks: current work item
   uint32_t flags[2];  // [0] hash table incomplete, [1] inconsistent input
+  uint32_t kth;       // hist_kth result
   uint32_t scratch[33];
   unsigned long long scratch64[33];
 };
@@ -516,7 +563,12 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   for (uint32_t i = n_hi + n_tie + tid; i < kq; i += blockDim.x) out[i] = 0ull;
 
   if (A.chunk_at && tid == 0) A.chunk_at[(unsigned long long)qi * A.n_groups + g] = at_f;
-  if (A.at_hint && tid == 0 && at_f >= 2) atomicMax(&A.at_hint[qi], at_f - 1);
+  if (A.at_hint && A.hint_hist) {
+    publish_seed(A.hint_hist + (size_t)qi * A.hint_stride, &A.at_hint[qi], cand, n_hi, n_tie, at_f, B,
+                 kq, scratch, &S.kth);
+  } else if (A.at_hint && tid == 0 && at_f >= 2) {
+    atomicMax(&A.at_hint[qi], at_f - 1);
+  }
   if (A.stats) {
     unsigned long long gsum = dev::block_sum((unsigned long long)n_gate, scratch64);
     unsigned long long isum = dev::block_sum((unsigned long long)n_ins, scratch64);

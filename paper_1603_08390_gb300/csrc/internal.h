@@ -19,13 +19,20 @@ void launch_exclusive_scan(uint32_t* v, uint32_t n, uint32_t* total, cudaStream_
 
 inline cudaStream_t as_stream(genie_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// Search over caller-owned device query arrays (search.cu).
+// Search over caller-owned device query arrays (search.cu).  at_hint: [n]
+// words; hint_hist: hint_hist_words words, used when they hold n x
+// (max_bound + 2) (per-query count histograms of the finished ranges).
 size_t search_scratch_bytes(const genie_index* idx, uint32_t max_bound, uint32_t n, uint32_t k);
 genie_status search_raw(const genie_index* idx, const uint32_t* q_off, const uint32_t* q_kw,
                         const uint32_t* bound, uint32_t n, uint32_t max_bound, uint32_t k,
                         const uint32_t* d_k, unsigned long long* cand, size_t cand_bytes,
-                        uint32_t* at_hint, uint32_t* ids, uint32_t* counts, uint32_t* n_valid,
-                        cudaStream_t s);
+                        uint32_t* at_hint, uint32_t* hint_hist, size_t hint_hist_words,
+                        uint32_t* ids, uint32_t* counts, uint32_t* n_valid, cudaStream_t s);
+
+// Largest per-query count histograms (bytes) a search allocates to seed the
+// AuditThreshold of later object ranges; beyond it the seed is the largest
+// k-th count of the finished ranges alone.
+constexpr uint64_t kHintHistMaxBytes = (uint64_t)256 << 20;
 
 }  // namespace genie
 

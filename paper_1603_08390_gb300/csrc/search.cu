@@ -91,11 +91,13 @@ cudaError_t dispatch_scan(const ScanArgs& a, const Plan& p, cudaStream_t s) {
                       : dispatch_width<4>(a, p, s);
 }
 
-// at_hint: [n_sel] zeroed device words shared by a query's ranges, or NULL
+// at_hint: [n_sel] zeroed device words shared by a query's ranges, or NULL;
+// hint_hist: [n_sel][p.za_len] zeroed words (the ranges' reported counts), or NULL
 cudaError_t run_pass(const genie_index* idx, const genie_queries* qs, uint32_t k, const uint32_t* d_k,
                      const uint32_t* seed, const uint32_t* sel, uint32_t n_sel, const Plan& p,
                      const genie_search_opts* o, unsigned long long* cand, uint32_t* at_hint,
-                     uint32_t* ids, uint32_t* counts, uint32_t* n_valid, cudaStream_t s) {
+                     uint32_t* hint_hist, uint32_t* ids, uint32_t* counts, uint32_t* n_valid,
+                     cudaStream_t s) {
   ScanArgs a;
   a.kw_off = idx->kw_off;
   a.post_ids = idx->post_ids;
@@ -120,6 +122,8 @@ cudaError_t run_pass(const genie_index* idx, const genie_queries* qs, uint32_t k
   a.chunk_at = (o && !sel) ? o->d_chunk_at : nullptr;
   a.stats = o ? o->d_stats : nullptr;
   a.at_hint = at_hint;
+  a.hint_hist = at_hint ? hint_hist : nullptr;
+  a.hint_stride = p.za_len;
   a.no_gate = (o && (o->flags & GENIE_SEARCH_NO_GATE)) ? 1u : 0u;
   const bool timed = o && !sel && o->scan_event_begin && o->scan_event_end;
   if (timed) cudaEventRecord((cudaEvent_t)o->scan_event_begin, s);
@@ -166,8 +170,8 @@ size_t search_scratch_bytes(const genie_index* idx, uint32_t max_bound, uint32_t
 genie_status search_raw(const genie_index* idx, const uint32_t* q_off, const uint32_t* q_kw,
                         const uint32_t* bound, uint32_t n, uint32_t max_bound, uint32_t k,
                         const uint32_t* d_k, unsigned long long* cand, size_t cand_bytes,
-                        uint32_t* at_hint, uint32_t* ids, uint32_t* counts, uint32_t* n_valid,
-                        cudaStream_t s) {
+                        uint32_t* at_hint, uint32_t* hint_hist, size_t hint_hist_words,
+                        uint32_t* ids, uint32_t* counts, uint32_t* n_valid, cudaStream_t s) {
   genie_queries view;
   view.index = idx;
   view.n_queries = n;
@@ -180,10 +184,13 @@ genie_status search_raw(const genie_index* idx, const uint32_t* q_off, const uin
   if (st != GENIE_OK) return st;
   if ((size_t)n * p.n_groups * k * 8 > cand_bytes)
     return fail(GENIE_ERR_CAPACITY, "search_raw: scratch too small");
+  if ((size_t)n * p.za_len > hint_hist_words) hint_hist = nullptr;
   cudaError_t e = at_hint ? cudaMemsetAsync(at_hint, 0, (size_t)n * 4, s) : cudaSuccess;
+  if (e == cudaSuccess && at_hint && hint_hist)
+    e = cudaMemsetAsync(hint_hist, 0, (size_t)n * p.za_len * 4, s);
   if (e == cudaSuccess)
-    e = run_pass(idx, &view, k, d_k, nullptr, nullptr, n, p, nullptr, cand, at_hint, ids, counts,
-                 n_valid, s);
+    e = run_pass(idx, &view, k, d_k, nullptr, nullptr, n, p, nullptr, cand, at_hint, hint_hist, ids,
+                 counts, n_valid, s);
   if (e != cudaSuccess) return fail_cuda(e, "search_raw");
   return GENIE_OK;
 }
@@ -209,9 +216,14 @@ extern "C" genie_status genie_search(const genie_index* index, const genie_queri
   const uint32_t Q = queries->n_queries;
   const uint64_t cand_bytes = (uint64_t)Q * p.n_groups * k * 8;
   unsigned long long* cand = nullptr;
-  uint32_t* aux = nullptr;  // [0] flags, [1] rerun count, [2..] rerun list
+  const bool share = !(opts && (opts->flags & GENIE_SEARCH_PER_RANGE_AT));
+  // per-query count histograms of the finished ranges, when they stay small
+  const uint64_t hist_words = (uint64_t)Q * p.za_len;
+  const bool use_hist = share && hist_words * 4 <= kHintHistMaxBytes;
+  uint32_t* aux = nullptr;  // [0] flags, [1] rerun count, [2..] rerun list, [Q] hints, histograms
   GENIE_CUDA_TRY(cudaMallocAsync((void**)&cand, cand_bytes, s));
-  cudaError_t e = cudaMallocAsync((void**)&aux, (uint64_t)(2 * Q + 2) * 4, s);
+  cudaError_t e =
+      cudaMallocAsync((void**)&aux, ((uint64_t)(2 * Q + 2) + (use_hist ? hist_words : 0)) * 4, s);
   if (e != cudaSuccess) {
     cudaFreeAsync(cand, s);
     return fail_cuda(e, "cudaMallocAsync");
@@ -232,12 +244,13 @@ extern "C" genie_status genie_search(const genie_index* index, const genie_queri
     if (bad) { release(); return fail(GENIE_ERR_INVALID_ARG, "genie_search: a per-query k is 0 or larger than k"); }
   }
   const uint32_t* seed = opts ? opts->d_seed : nullptr;
-  const bool share = !(opts && (opts->flags & GENIE_SEARCH_PER_RANGE_AT));
-  uint32_t* hint = share ? aux + 2 + Q : nullptr;  // [Q]: largest k-th count of finished ranges
+  uint32_t* hint = share ? aux + 2 + Q : nullptr;  // [Q]: seeds from the finished ranges
+  uint32_t* hist = use_hist ? aux + 2 + 2 * Q : nullptr;
   e = hint ? cudaMemsetAsync(hint, 0, (size_t)Q * 4, s) : cudaSuccess;
+  if (e == cudaSuccess && hist) e = cudaMemsetAsync(hist, 0, hist_words * 4, s);
   if (e == cudaSuccess)
-    e = run_pass(index, queries, k, d_k, seed, nullptr, Q, p, opts, cand, hint, d_ids, d_counts,
-                 d_n_valid, s);
+    e = run_pass(index, queries, k, d_k, seed, nullptr, Q, p, opts, cand, hint, hist, d_ids,
+                 d_counts, d_n_valid, s);
   if (e == cudaSuccess && seed) {
     // verify-and-rerun: certified iff s = 1 or the k-th merged count >= s
     uint32_t n_rerun = 0;
@@ -251,9 +264,10 @@ extern "C" genie_status genie_search(const genie_index* index, const genie_queri
     if (e == cudaSuccess && n_rerun > 0) {
       if (opts && opts->d_stats) add_stat_kernel<<<1, 1, 0, s>>>(opts->d_stats + 3, n_rerun);
       e = hint ? cudaMemsetAsync(hint, 0, (size_t)n_rerun * 4, s) : cudaSuccess;
+      if (e == cudaSuccess && hist) e = cudaMemsetAsync(hist, 0, (size_t)n_rerun * p.za_len * 4, s);
       if (e == cudaSuccess)
-        e = run_pass(index, queries, k, d_k, nullptr, aux + 2, n_rerun, p, opts, cand, hint, d_ids,
-                     d_counts, d_n_valid, s);
+        e = run_pass(index, queries, k, d_k, nullptr, aux + 2, n_rerun, p, opts, cand, hint, hist,
+                     d_ids, d_counts, d_n_valid, s);
     }
   }
   release();
@@ -356,8 +370,8 @@ extern "C" genie_status genie_search_noalloc(const genie_index* index, const gen
   uint32_t* hint = share ? reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(base) + cand_bytes)
                          : nullptr;
   if (hint) GENIE_CUDA_TRY(cudaMemsetAsync(hint, 0, hint_bytes, s));
-  cudaError_t e = run_pass(index, queries, k, d_k, nullptr, nullptr, Q, p, opts, cand, hint, d_ids,
-                           d_counts, d_n_valid, s);
+  cudaError_t e = run_pass(index, queries, k, d_k, nullptr, nullptr, Q, p, opts, cand, hint, nullptr,
+                           d_ids, d_counts, d_n_valid, s);
   if (e != cudaSuccess) return fail_cuda(e, "genie_search_noalloc");
   return GENIE_OK;
 }

@@ -55,6 +55,8 @@ struct Slot {
   unsigned long long* cand = nullptr;
   size_t cand_bytes = 0;
   uint32_t* hint = nullptr;
+  uint32_t* hint_hist = nullptr;  // per-query count histograms of the finished ranges
+  size_t hint_hist_words = 0;
   uint32_t *h_q_off = nullptr, *h_q_kw = nullptr, *h_bound = nullptr, *h_karr = nullptr;
   uint32_t *h_ids = nullptr, *h_counts = nullptr, *h_n_valid = nullptr;
   std::vector<Request> reqs;
@@ -98,6 +100,7 @@ void free_slot(Slot& s) {
   cudaFree(s.n_valid);
   cudaFree(s.cand);
   cudaFree(s.hint);
+  cudaFree(s.hint_hist);
   cudaFreeHost(s.h_q_off);
   cudaFreeHost(s.h_q_kw);
   cudaFreeHost(s.h_bound);
@@ -127,7 +130,8 @@ void launch_slot(genie_server* sv, Slot& s) {
   cudaMemcpyAsync(s.bound, s.h_bound, n * 4, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(s.karr, s.h_karr, n * 4, cudaMemcpyHostToDevice, st);
   genie_status gs = search_raw(sv->index, s.q_off, s.q_kw, s.bound, n, max_bound, kmax, s.karr,
-                               s.cand, s.cand_bytes, s.hint, s.ids, s.counts, s.n_valid, st);
+                               s.cand, s.cand_bytes, s.hint, s.hint_hist, s.hint_hist_words, s.ids,
+                               s.counts, s.n_valid, st);
   if (gs != GENIE_OK) sv->error = gs;
   cudaMemcpyAsync(s.h_ids, s.ids, (size_t)n * kmax * 4, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(s.h_counts, s.counts, (size_t)n * kmax * 4, cudaMemcpyDeviceToHost, st);
@@ -265,6 +269,12 @@ extern "C" genie_status genie_server_create(const genie_index* index, const geni
     if (e == cudaSuccess) e = cudaMalloc(&s.n_valid, o.max_batch * 4);
     if (e == cudaSuccess) e = cudaMalloc(&s.cand, cand);
     if (e == cudaSuccess) e = cudaMalloc(&s.hint, o.max_batch * 4);
+    const size_t hist_words =
+        (size_t)o.max_batch * (std::min<uint32_t>(o.max_query_keywords, GENIE_MAX_BOUND) + 2);
+    if (e == cudaSuccess && hist_words * 4 <= kHintHistMaxBytes) {
+      e = cudaMalloc(&s.hint_hist, hist_words * 4);
+      s.hint_hist_words = hist_words;
+    }
     s.cand_bytes = cand;
     if (e == cudaSuccess) e = cudaMallocHost(&s.h_q_off, (o.max_batch + 1) * 4);
     if (e == cudaSuccess) e = cudaMallocHost(&s.h_q_kw, kw_cap * 4);
