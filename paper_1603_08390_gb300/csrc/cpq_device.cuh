@@ -297,7 +297,6 @@ __device__ __noinline__ void publish_seed(uint32_t* hh, uint32_t* seed,
 struct BlockShared {
   uint32_t at;        // AuditThreshold
   uint32_t n;         // read-out counter
-  uint32_t next;      // next tile of the current keyword batch
   uint32_t item;      // persistent blocks: current work item
   uint32_t flags[2];  // [0] hash table incomplete, [1] inconsistent input
   uint32_t kth;       // hist_kth result
@@ -318,7 +317,6 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   constexpr uint32_t kUnroll = U, kTile = 32 * 4 * U;
   uint32_t& s_at = S.at;
   uint32_t& s_n = S.n;
-  uint32_t& s_next = S.next;
   uint32_t* s_flags = S.flags;
   uint32_t* scratch = S.scratch;
   unsigned long long* scratch64 = S.scratch64;
@@ -388,12 +386,11 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     uint32_t pre = dev::block_exclusive_scan(ntiles, scratch, &total_tiles);
     if (tid < nk) tile_pre[tid] = pre;
     if (tid == 0) tile_pre[nk] = total_tiles;  // sentinel for the segment cursor
-    if (tid == 0) s_next = 2 * nwarps;
     __syncthreads();
 
-    // Warps take runs of kRun consecutive tiles from a shared counter (warps
-    // slowed by Gate work take fewer runs); a warp's tile numbers only grow,
-    // so its segment cursor j only moves forward.
+    // Warp w takes the runs of kRun consecutive tiles w, w + nwarps, ...
+    // (interleaved, so long lists spread over all warps); its tile numbers
+    // only grow, so its segment cursor j only moves forward.
     uint32_t j = 0;
     auto locate_load = [&](uint32_t tt, uint32_t& lo_, uint32_t& hi_, uint32_t& st_,
                            uint4 (&vv)[U]) {
@@ -411,19 +408,18 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     };
     // With two loads per lane the next tile is located and loaded while this
     // one's counter updates are in flight (more registers would spill with
-    // four); the next run is claimed one run ahead.
+    // four).
     constexpr bool kPrefetch = U == 2;
-    uint32_t t = warp * kRun, t_end = min(t + kRun, total_tiles);
-    uint32_t pending = nwarps + warp;  // the run after the current one
+    uint32_t run = warp, t = run * kRun, t_end = min(t + kRun, total_tiles);
     uint32_t lo = 0, hi = 0, start = 0;
     uint4 v[kUnroll];
     if (kPrefetch && t < total_tiles) locate_load(t, lo, hi, start, v);
     while (t < total_tiles) {
-      // the tile after t: the next of this run, else the first of the pending run
+      // the tile after t: the next of this run, else the first of the warp's next run
       const bool run_ends = t + 1 >= t_end;
-      const uint32_t tn = run_ends ? pending * kRun : t + 1;
+      const uint32_t tn = run_ends ? (run + nwarps) * kRun : t + 1;
       const uint32_t tn_end = run_ends ? min(tn + kRun, total_tiles) : t_end;
-      uint32_t claim = 0, lo1 = 0, hi1 = 0, start1 = 0;
+      uint32_t lo1 = 0, hi1 = 0, start1 = 0;
       uint4 v1[kUnroll];
       if (!kPrefetch) locate_load(t, lo, hi, start, v);
       // slots inside the list: four bits per 16-byte vector
@@ -457,7 +453,6 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
                                       Lane<LOG2W>::inc(id));
         }
       }
-      if (run_ends && lane == 0) claim = atomicAdd(&s_next, 1u);  // the run after pending
       if (kPrefetch) {
 #pragma unroll
         for (uint32_t u = 0; u < kUnroll; ++u) v1[u] = make_uint4(0, 0, 0, 0);
@@ -492,7 +487,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
           }
         }
       }
-      if (run_ends) pending = __shfl_sync(0xFFFFFFFFu, claim, 0);
+      if (run_ends) run += nwarps;
       t = tn;
       t_end = tn_end;
       if (kPrefetch) {
