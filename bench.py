@@ -152,9 +152,21 @@ class Clocks:
                 "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
 
 
-def traffic_from_profile(kernel_src: str):
+KERNEL_SOURCES = ("cpq_device.cuh", "device_util.cuh", "search.cu")
+
+
+def kernel_source_sha() -> str:
+    """sha256 of the scan kernel's sources, concatenated in KERNEL_SOURCES order."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1603_08390_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def traffic_from_profile():
     """Per-launch DRAM bytes of the scan kernel from the committed ncu summary,
-    valid only while the kernel source is unchanged since the capture."""
+    valid only while the kernel sources are unchanged since the capture."""
     p = os.path.join(ROOT, "profiles", "scan_cpq_lsh1m_ncu.md")
     if not os.path.exists(p):
         return None
@@ -164,9 +176,7 @@ def traffic_from_profile(kernel_src: str):
     m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
     if not m_sha or not m_b:
         return None
-    with open(kernel_src, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()
-    return float(m_b.group(1)) if sha == m_sha.group(1) else None
+    return float(m_b.group(1)) if kernel_source_sha() == m_sha.group(1) else None
 
 
 def cpu_baseline(w, n_sample: int) -> dict:
@@ -328,7 +338,6 @@ def run_genie(args, rank, world, local):
     peak, peak_kind = measured_peaks()
     algo_bytes = 4.0 * entries  # one 4-byte object id read per posting scanned
     achieved = algo_bytes / (scan_ms / 1e3) / 1e9
-    src = os.path.join(ROOT, "paper_1603_08390_gb300", "csrc", "search.cu")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -338,8 +347,8 @@ def run_genie(args, rank, world, local):
         "latency_ms": {"batch_p50": float(np.percentile(per_step, 50)),
                        "batch_p99": float(np.percentile(per_step, 99))},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic_from_profile(src),
-                     "kernel": "scan_cpq_kernel<4>", "peak_kind": peak_kind + " hbm_gbs",
+                     "frac": achieved / peak, "traffic": traffic_from_profile(),
+                     "kernel": "scan_cpq_kernel<4, 2, 768>", "peak_kind": peak_kind + " hbm_gbs",
                      "scan_ms": scan_ms, "algorithmic_bytes_per_launch": algo_bytes},
         "smem_atomic_roofline": {
             "bound": "shared-memory atomic adds (one per posting)",
