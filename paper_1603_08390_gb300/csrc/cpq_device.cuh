@@ -122,37 +122,46 @@ __device__ __forceinline__ uint32_t atom_add_shared_if(uint32_t p, uint32_t sadd
 }
 
 // First `limit` lanes (ascending id) whose count equals `value` (or is at
-// least `value` when AT_LEAST) become result keys dst[0..); returns how many.
+// least `value` when AT_LEAST; value >= 1) become result keys dst[0..);
+// returns how many.  Each thread reads four counter words per round; the
+// rounds stop once `limit` lanes are found.  Words between nwords and the next
+// multiple of four must exist and be zero.  All threads of the block call it.
 template <int LOG2W, bool AT_LEAST>
 __device__ uint32_t collect_lanes(const uint32_t* bc, uint32_t nwords, uint32_t value,
                                   uint32_t limit, uint32_t obj_base, unsigned long long* dst,
                                   uint32_t* scratch) {
   constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, MASK = (1u << W) - 1u;
-  const uint32_t per = (nwords + blockDim.x - 1) / blockDim.x;
-  const uint32_t wa = min(nwords, threadIdx.x * per), wb = min(nwords, wa + per);
-  uint32_t m = 0;
-  for (uint32_t w = wa; w < wb; ++w) {
-    uint32_t word = bc[w];
+  const uint32_t nw4 = (nwords + 3) & ~3u;
+  uint32_t found = 0;
+  for (uint32_t r0 = 0; r0 < nw4 && found < limit; r0 += 4 * blockDim.x) {
+    const uint32_t w0 = r0 + 4 * threadIdx.x;
+    const uint4 q = w0 < nw4 ? *reinterpret_cast<const uint4*>(bc + w0) : make_uint4(0, 0, 0, 0);
+    const uint32_t words[4] = {q.x, q.y, q.z, q.w};
+    uint32_t m = 0;
 #pragma unroll
-    for (uint32_t l = 0; l < PER; ++l) {
-      uint32_t v = (word >> (l * W)) & MASK;
-      m += AT_LEAST ? (v >= value) : (v == value);
-    }
-  }
-  uint32_t total;
-  uint32_t pos = dev::block_exclusive_scan(m, scratch, &total);
-  if (pos < limit) {
-    for (uint32_t w = wa; w < wb && pos < limit; ++w) {
-      uint32_t word = bc[w];
+    for (uint32_t e = 0; e < 4; ++e) {
 #pragma unroll
       for (uint32_t l = 0; l < PER; ++l) {
-        uint32_t v = (word >> (l * W)) & MASK;
-        if ((AT_LEAST ? (v >= value) : (v == value)) && pos < limit)
-          dst[pos++] = dev::result_key(v, obj_base + w * PER + l);
+        const uint32_t v = (words[e] >> (l * W)) & MASK;
+        m += AT_LEAST ? (v >= value) : (v == value);
       }
     }
+    uint32_t total;
+    uint32_t pos = found + dev::block_exclusive_scan(m, scratch, &total);
+    if (m && pos < limit) {
+#pragma unroll
+      for (uint32_t e = 0; e < 4; ++e) {
+#pragma unroll
+        for (uint32_t l = 0; l < PER; ++l) {
+          const uint32_t v = (words[e] >> (l * W)) & MASK;
+          if ((AT_LEAST ? (v >= value) : (v == value)) && pos < limit)
+            dst[pos++] = dev::result_key(v, obj_base + (w0 + e) * PER + l);
+        }
+      }
+    }
+    found += total;
   }
-  return min(total, limit);
+  return min(found, limit);
 }
 
 // Number of lanes whose count is at least `value` (all threads of the block).
@@ -543,13 +552,14 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   if (!certified)  // Bitmap-Counter selection of the same set
     n_hi = collect_lanes<LOG2W, true>(bc, nwords_local, at_f, kq, obj_base, cand, scratch);
   __syncthreads();
-  {
-    const uint32_t n2 = dev::next_pow2(max(n_hi, 1u));
-    for (uint32_t i = n_hi + tid; i < n2; i += blockDim.x) cand[i] = 0ull;
-    __syncthreads();
-    dev::bitonic_sort_desc(cand, n2);
+  // the keys are distinct (one per object): each goes straight to its rank in
+  // (count desc, id asc) order
+  for (uint32_t i = tid; i < n_hi; i += blockDim.x) {
+    const unsigned long long key = cand[i];
+    uint32_t r = 0;
+    for (uint32_t j = 0; j < n_hi; ++j) r += cand[j] > key;
+    out[r] = key;
   }
-  for (uint32_t i = tid; i < n_hi; i += blockDim.x) out[i] = cand[i];
   // ties at the k-th count, ascending id, from the Bitmap Counter
   uint32_t n_tie = 0;
   if (at_f >= 2 && n_hi < kq)
