@@ -283,19 +283,32 @@ __device__ __forceinline__ uint32_t hist_kth(const uint32_t* h, uint32_t B, uint
   return 0;
 }
 
-// Adds a finished range's reported counts (cand[0..n_hi) and n_tie ties at
-// at_f - 1) to its query's histogram hh, then raises the query's seed to the
-// k-th largest count of everything its finished ranges reported.  All
-// threads of the block call it.
+// Adds the counts a finished range reports (cand[0..n_hi) and n_tie ties at
+// at_f - 1) that lie above the query's current seed to the query's histogram
+// hh, then raises the seed to the k-th largest count the histogram holds.
+// The histogram counts a subset of the reported objects, so that k-th
+// largest is still at most the query's k-th count; counts at or below the
+// current seed cannot raise it and are left out.  All threads of the block
+// call it.
 __device__ __noinline__ void publish_seed(uint32_t* hh, uint32_t* seed,
                                           const unsigned long long* cand, uint32_t n_hi,
                                           uint32_t n_tie, uint32_t at_f, uint32_t B, uint32_t k,
                                           uint32_t* scratch, uint32_t* s_res) {
-  for (uint32_t i = threadIdx.x; i < n_hi; i += blockDim.x)
-    atomicAdd(&hh[dev::key_count(cand[i])], 1u);
-  if (threadIdx.x == 0 && n_tie) atomicAdd(&hh[at_f - 1], n_tie);
+  const uint32_t h0 = *(volatile uint32_t*)seed;
+  int added = 0;
+  for (uint32_t i = threadIdx.x; i < n_hi; i += blockDim.x) {
+    const uint32_t c = dev::key_count(cand[i]);
+    if (c > h0) {
+      atomicAdd(&hh[c], 1u);
+      added = 1;
+    }
+  }
+  if (threadIdx.x == 0 && n_tie && at_f - 1 > h0) {
+    atomicAdd(&hh[at_f - 1], n_tie);
+    added = 1;
+  }
   __threadfence();
-  __syncthreads();
+  if (!__syncthreads_or(added)) return;
   const uint32_t x = hist_kth(hh, B, k, scratch, *s_res);
   if (threadIdx.x == 0 && x) atomicMax(seed, x);
 }
@@ -309,6 +322,8 @@ struct BlockShared {
   uint32_t item;      // persistent blocks: current work item
   uint32_t flags[2];  // [0] hash table incomplete, [1] inconsistent input
   uint32_t kth;       // hist_kth result
+  uint32_t at0;       // AuditThreshold the range started with
+  uint32_t tie_floor; // ties below it are left out of the read-out
   uint32_t scratch[33];
   unsigned long long scratch64[33];
 };
@@ -364,6 +379,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
       uint32_t s0 = A.seed ? A.seed[q] : 1u;
       if (A.at_hint) s0 = max(s0, vld(&A.at_hint[qi]));
       s_at = max(1u, min(s0, B + 1));
+      S.at0 = s_at;
       s_flags[0] = 0;
       s_flags[1] = 0;
     }
@@ -530,6 +546,11 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     s_at = a;
     s_n = 0;
   }
+  // A seed (the starting AT, or the query's current one, which other blocks
+  // may be raising) is at most the query's k-th count, so ties below it
+  // cannot reach the query's top-k.  One thread reads it: every thread must
+  // take the same branch around the block-wide tie collection.
+  if (tid == 0) S.tie_floor = max(S.at0, A.at_hint ? vld(&A.at_hint[qi]) : 0u);
   __syncthreads();
   const uint32_t at_f = s_at;
   unsigned long long* out = A.cand + ((unsigned long long)qi * A.n_groups + g) * A.k;
@@ -560,9 +581,11 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     for (uint32_t j = 0; j < n_hi; ++j) r += cand[j] > key;
     out[r] = key;
   }
-  // ties at the k-th count, ascending id, from the Bitmap Counter
+  // ties at the k-th count, ascending id, from the Bitmap Counter; below the
+  // tie floor they are left out (the range then reports only its objects at
+  // or above AT_f)
   uint32_t n_tie = 0;
-  if (at_f >= 2 && n_hi < kq)
+  if (at_f >= 2 && n_hi < kq && at_f - 1 >= S.tie_floor)
     n_tie = collect_lanes<LOG2W, false>(bc, nwords_local, at_f - 1, kq - n_hi, obj_base,
                                         out + n_hi, scratch);
   for (uint32_t i = n_hi + n_tie + tid; i < kq; i += blockDim.x) out[i] = 0ull;
