@@ -57,7 +57,7 @@ struct ScanArgs {
 
 constexpr uint32_t kMaxProbe = 32;   // hash-table probes before an insert gives up
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
-constexpr uint32_t kTilePrePad = 4;  // tile prefix sums: the sentinel after the last keyword
+constexpr uint32_t kTilePrePad = 36;  // tile prefix sums: sentinels read by a warp-wide step
 constexpr uint32_t kRun = 4;         // consecutive tiles a warp takes per claim
 
 size_t scan_smem_bytes(uint32_t log2w, uint32_t block_shift, uint32_t ht_slots, uint32_t za_len,
@@ -410,16 +410,25 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     uint32_t total_tiles;
     uint32_t pre = dev::block_exclusive_scan(ntiles, scratch, &total_tiles);
     if (tid < nk) tile_pre[tid] = pre;
-    if (tid == 0) tile_pre[nk] = total_tiles;  // sentinel for the segment cursor
+    // after the last keyword: the tile count, then entries no tile reaches
+    if (tid <= 32) tile_pre[nk + tid] = tid == 0 ? total_tiles : 0xFFFFFFFFu;
     __syncthreads();
 
     // Warp w takes the runs of kRun consecutive tiles w, w + nwarps, ...
     // (interleaved, so long lists spread over all warps); its tile numbers
-    // only grow, so its segment cursor j only moves forward.
+    // only grow, so its segment cursor j only moves forward: by one test
+    // inside a run, by 32 segments per warp-wide step when it jumps to the
+    // warp's next run.
     uint32_t j = 0;
     auto locate_load = [&](uint32_t tt, uint32_t& lo_, uint32_t& hi_, uint32_t& st_,
                            uint4 (&vv)[U]) {
-      while (tile_pre[j + 1] <= tt) ++j;
+      if (tile_pre[j + 1] <= tt) {
+        for (;;) {
+          const uint32_t ball = __ballot_sync(0xFFFFFFFFu, tile_pre[j + 1 + lane] <= tt);
+          j += __popc(ball);  // tile_pre is non-decreasing: the ballot is a prefix
+          if (ball != 0xFFFFFFFFu) break;
+        }
+      }
       const uint2 sg = seg[j];
       lo_ = sg.x;
       hi_ = sg.y;
