@@ -330,7 +330,8 @@ def run_genie(args, rank, world, local):
                        opts=genie.make_opts(d_stats=stats), stream=stream)
     st = stats.cpu().numpy()
     cpq = {"gate_passes_per_posting": float(st[0]) / entries, "ht_inserts": int(st[1]),
-           "blocks": int(st[4]), "blocks_bitmap_fallback": int(st[2]), "bad_ids": int(st[5])}
+           "blocks": int(st[4]), "blocks_bitmap_fallback": int(st[2]),
+           "blocks_gateless_unseeded": int(st[6]), "bad_ids": int(st[5])}
     del qs
 
     if rank != 0:

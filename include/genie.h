@@ -209,8 +209,12 @@ typedef struct {
    *   d_chunk_at    [n_queries * n_blocks_per_query] uint32: final
    *                 AuditThreshold of each (query, object range) block;
    *   d_stats       [8] uint64 accumulated: 0 gate passes, 1 hash-table
-   *                 inserts, 2 blocks that fell back to a Bitmap-Counter
-   *                 selection, 3 seeded queries rerun, 4 blocks launched. */
+   *                 inserts, 2 blocks whose hash-table read-out was not
+   *                 certified and fell back to a Bitmap-Counter selection,
+   *                 3 seeded queries rerun, 4 blocks launched, 5 blocks that
+   *                 saw a count above the query's bound (inconsistent input),
+   *                 6 blocks that started without a seed and selected from
+   *                 the Bitmap Counter without running the Gate. */
   uint32_t* d_chunk_at;
   unsigned long long* d_stats;
   /* Output: number of object ranges per query used (host pointer, may be NULL). */

@@ -323,6 +323,7 @@ struct BlockShared {
   uint32_t flags[2];  // [0] hash table incomplete, [1] inconsistent input
   uint32_t kth;       // hist_kth result
   uint32_t at0;       // AuditThreshold the range started with
+  uint32_t gateless;  // count only, then select from the Bitmap Counter
   uint32_t tie_floor; // ties below it are left out of the read-out
   uint32_t scratch[33];
   unsigned long long scratch64[33];
@@ -380,11 +381,17 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
       if (A.at_hint) s0 = max(s0, vld(&A.at_hint[qi]));
       s_at = max(1u, min(s0, B + 1));
       S.at0 = s_at;
+      // A range that starts before any range of its query has finished (no
+      // seed yet) would run the Gate from AT = 1 through every level; its
+      // k-th count is selected from the Bitmap Counter after counting
+      // instead, and the ranges after it run the Gate from its seed.
+      S.gateless = A.no_gate || (A.at_hint && s_at == 1);
       s_flags[0] = 0;
       s_flags[1] = 0;
     }
   }
   __syncthreads();
+  const bool gateless = S.gateless;
 
   uint32_t n_gate = 0, n_ins = 0;
 
@@ -503,7 +510,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
       // Gate (Algorithm 1, lines 3-7) for the postings whose new count val + 1
       // reaches the (possibly stale) AuditThreshold: rare, so a tile is tested
       // once on each lane's largest count.
-      const uint32_t at_c = A.no_gate ? 0xFFFFFFFFu : vld(&s_at);
+      const uint32_t at_c = gateless ? 0xFFFFFFFFu : vld(&s_at);
       if (__any_sync(0xFFFFFFFFu, vmax + 1 >= at_c)) {
         uint32_t pm = 0;  // this lane's passing slots
 #pragma unroll
@@ -537,7 +544,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
 
   // ---- finalise AT (Lemma 3.1) and read out this range's top-k ----------
   const uint32_t nwords_local = (n_local + PER - 1) / PER;
-  if (A.no_gate) {
+  if (gateless) {
     // the k-th count of the range: largest x with #{count >= x} >= k
     uint32_t lo_x = 0, hi_x = B;
     while (lo_x < hi_x) {
@@ -578,7 +585,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   }
   __syncthreads();
   uint32_t n_hi = s_n;
-  const bool certified = !A.no_gate && !s_flags[0] && n_hi == want && n_hi < kq;
+  const bool certified = !gateless && !s_flags[0] && n_hi == want && n_hi < kq;
   if (!certified)  // Bitmap-Counter selection of the same set
     n_hi = collect_lanes<LOG2W, true>(bc, nwords_local, at_f, kq, obj_base, cand, scratch);
   __syncthreads();
@@ -612,7 +619,8 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     if (tid == 0) {
       atomicAdd(&A.stats[0], gsum);
       atomicAdd(&A.stats[1], isum);
-      if (!certified) atomicAdd(&A.stats[2], 1ull);
+      if (!certified && !gateless) atomicAdd(&A.stats[2], 1ull);
+      if (gateless) atomicAdd(&A.stats[6], 1ull);
       atomicAdd(&A.stats[4], 1ull);
       if (s_flags[1]) atomicAdd(&A.stats[5], 1ull);
     }

@@ -118,10 +118,12 @@ def test_learned_seeds_keep_results_exact_and_cut_gate_work():
     p = yv - np.float32(tr["margin"])
     want = np.where(p >= 1, np.minimum(np.floor(p), feats["bound"] + 1), 1).astype(np.uint32)
     assert np.array_equal(runner.u32(seeds), want)
-    # exact results, fewer Gate passes than the plain search
+    # exact results, and fewer Gate passes than c-PQ run from AT = 1 in every
+    # object range (the plain search with per-range AT)
     st_plain = torch.zeros(8, dtype=torch.int64, device="cuda")
     st_seed = torch.zeros(8, dtype=torch.int64, device="cuda")
-    plain = runner.search(idx, qs, 20, opts=genie.make_opts(d_stats=st_plain)).host()
+    plain = runner.search(idx, qs, 20, opts=genie.make_opts(
+        d_stats=st_plain, flags=genie.GENIE_SEARCH_PER_RANGE_AT)).host()
     seeded = learned.seeded_search(idx, qs, tr["mlp"], tr["margin"], 20, stats=st_seed).host()
     torch.cuda.synchronize()
     ref_res = oracle.topk(w)

@@ -235,13 +235,16 @@ def test_two_streams_share_one_index():
 def test_hash_table_overflow_falls_back_exactly():
     w = synth.lsh(80_000, 24, 100, config=22)
     stats = torch.zeros(8, dtype=torch.int64, device="cuda")
+    # per-range AT: every block runs the Gate, so the fallback is the hash table's
     res, _, _ = run(w, chunk_shift=13, opts=genie.make_opts(block_shift=13, ht_slots=32,
-                                                             d_stats=stats))
+                                                             d_stats=stats,
+                                                             flags=genie.GENIE_SEARCH_PER_RANGE_AT))
     assert_same(res, oracle.topk(w))
     st = stats.cpu().numpy()
     assert st[4] == w.n_queries * ((w.n_objects + 8191) >> 13)
     assert st[2] > 0  # the Bitmap-Counter selection ran
     assert st[5] == 0  # no inconsistent ids
+    assert st[6] == 0  # no block skipped the Gate
 
 
 def test_seeded_gate_verify_and_rerun():
