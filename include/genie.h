@@ -499,6 +499,71 @@ genie_status genie_search_noalloc(const genie_index* index, const genie_queries*
                                   uint32_t* d_ids, uint32_t* d_counts, uint32_t* d_n_valid,
                                   genie_stream stream);
 
+/* ------------------------------------------------------------------------ */
+/* Multiple loadings (Sec. 3.4; Tables 3-4): an index in parts held in host  */
+/* memory                                                                    */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * When the index of all objects does not fit in device memory, the objects
+ * are split into parts by id; each part gets its own index, the parts wait in
+ * (pinned) host memory, and a query batch is run against the parts one after
+ * the other, its per-part top-k lists being merged (Sec. 3.4).  A part store
+ * keeps two device slots sized for its largest part; while the batch runs on
+ * part p, part p + 1 is copied into the other slot on a second stream.
+ */
+typedef struct genie_parts genie_parts;
+
+typedef struct {
+  uint32_t n_parts;
+  uint32_t vocab;
+  uint32_t n_objects;       /* one past the largest global object id */
+  uint32_t reserved;
+  uint64_t host_bytes;      /* pinned host memory held by the parts */
+  uint64_t max_part_bytes;  /* bytes of the largest part (one device slot) */
+} genie_parts_info;
+
+/* An empty part store (library-owned; free it with genie_parts_destroy). */
+genie_status genie_parts_create(genie_parts** out);
+
+/* Release a part store and its host and device memory (NULL is ignored).
+   Synchronises the device. */
+void genie_parts_destroy(genie_parts* parts);
+
+/*
+ * Append a part: copy `index` (built by genie_build_index over the part's
+ * objects, numbered 0 .. n - 1) into new pinned host memory; its objects get
+ * the global ids id_base .. id_base + n - 1.  The index is not changed and
+ * may be destroyed after the call.  Parts must be added in ascending,
+ * disjoint id ranges and share one vocabulary; id_base + n must stay below
+ * 2^32 - 1.  Synchronises `stream`.  Errors: INVALID_ARG (order, overlap,
+ * vocabulary, id range), OUT_OF_MEMORY, CUDA.
+ */
+genie_status genie_parts_add(genie_parts* parts, const genie_index* index, uint32_t id_base,
+                             genie_stream stream);
+
+genie_status genie_parts_get_info(const genie_parts* parts, genie_parts_info* out);
+
+/*
+ * Top-k of every query over all parts.
+ *   d_q_off [n_queries+1], d_q_kw: keyword queries, as for genie_make_queries
+ *                (device; read once per part).
+ *   k, d_k, d_ids, d_counts, d_n_valid: as for genie_search; ids are global.
+ * Each part is loaded into a device slot (the first on the call, the next
+ * ones overlapped with the search of the one before), its queries are
+ * compiled and searched as by genie_make_queries + genie_search, and the
+ * per-part lists are merged on the device.  Results equal those of one index
+ * over all objects: ids in (count desc, id asc) order, unused slots id
+ * 0xFFFFFFFF and count 0.  Synchronises `stream` once per part (the query
+ * compile) and waits for the copy stream before it returns.  Calls on one
+ * store must not overlap (they share its device slots).  Errors: as for
+ * genie_make_queries and genie_search; INVALID_ARG if the store has no part.
+ */
+genie_status genie_parts_search(genie_parts* parts, const uint32_t* d_q_off, const uint32_t* d_q_kw,
+                                uint32_t n_queries, uint32_t k, const uint32_t* d_k,
+                                uint32_t* d_ids, uint32_t* d_counts, uint32_t* d_n_valid,
+                                genie_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,314 @@
+// Multiple loadings (Sec. 3.4): an index split into parts by object id, held
+// in pinned host memory, and searched one part at a time.
+//
+// The paper loads the parts of an index that does not fit in device memory
+// one after the other, runs the whole query batch on each, and merges the
+// per-part top-k lists on the CPU (Tables 3-4).  Here every part is a normal
+// index whose arrays were copied to pinned host memory.  A search keeps two
+// device slots: while the queries run against part p in one slot, a second
+// stream copies part p + 1 into the other.  Each part's search is the usual
+// one (compile, scan + c-PQ, per-range merge) and writes that part's top-k;
+// the per-part lists then become result keys with global object ids and go
+// through the same device merge as the object ranges of one index.  The merge
+// is exact under (count desc, id asc): the batch's top-k is a subset of the
+// union of the parts' top-k lists, and parts come in ascending id order, so
+// ties at the k-th count are taken in ascending id.
+#include <algorithm>
+#include <vector>
+
+#include "cpq_device.cuh"
+#include "device_util.cuh"
+#include "internal.h"
+
+namespace genie {
+namespace {
+
+struct HostPart {
+  uint32_t base = 0;  // global id of the part's object 0
+  uint32_t n_objects = 0, max_object_len = 0, chunk_shift = 0, n_chunks = 0;
+  uint64_t nnz = 0, post_len = 0, chunk_len = 0;
+  uint64_t* kw_off = nullptr;    // pinned host copies of the index arrays
+  uint32_t* post_ids = nullptr;
+  uint32_t* chunk_pos = nullptr;
+};
+
+// part outputs [P][Q][k] -> result keys [Q][P][k] with global ids (0 past n_valid)
+__global__ void part_keys_kernel(const uint32_t* __restrict__ ids, const uint32_t* __restrict__ counts,
+                                 const uint32_t* __restrict__ n_valid,
+                                 const uint32_t* __restrict__ bases, uint32_t P, uint32_t Q,
+                                 uint32_t k, unsigned long long* __restrict__ keys) {
+  const uint64_t total = (uint64_t)P * Q * k;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = (uint32_t)(i % k);
+    const uint64_t pq = i / k;  // p * Q + q
+    const uint32_t p = (uint32_t)(pq / Q), q = (uint32_t)(pq % Q);
+    unsigned long long key = 0;
+    if (j < n_valid[pq]) key = dev::result_key(counts[i], bases[p] + ids[i]);
+    keys[((uint64_t)q * P + p) * k + j] = key;
+  }
+}
+
+__global__ void max_bound_kernel(const uint32_t* __restrict__ b, uint32_t n,
+                                 uint32_t* __restrict__ acc) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    acc[i] = max(acc[i], b[i]);
+}
+
+uint32_t grid_for(uint64_t n, uint32_t threads) {
+  return (uint32_t)std::min<uint64_t>((n + threads - 1) / threads, 152ull * 32);
+}
+
+}  // namespace
+}  // namespace genie
+
+using namespace genie;
+
+struct genie_parts {
+  int device = 0;
+  uint32_t vocab = 0;
+  std::vector<HostPart> parts;
+  // two device slots, each a complete index view sized for the largest part
+  genie_index slot[2];
+  uint64_t slot_post_cap = 0, slot_chunk_cap = 0;
+  cudaStream_t copy = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+void free_slots(genie_parts* ps) {
+  for (genie_index& s : ps->slot) {
+    cudaFree(s.kw_off);
+    cudaFree(s.post_ids);
+    cudaFree(s.chunk_pos);
+    s.kw_off = nullptr;
+    s.post_ids = nullptr;
+    s.chunk_pos = nullptr;
+  }
+  ps->slot_post_cap = ps->slot_chunk_cap = 0;
+}
+
+// device slots large enough for every part
+cudaError_t ensure_slots(genie_parts* ps) {
+  uint64_t post = 0, chunk = 0;
+  for (const HostPart& h : ps->parts) {
+    post = std::max(post, h.post_len);
+    chunk = std::max(chunk, h.chunk_len);
+  }
+  if (post <= ps->slot_post_cap && chunk <= ps->slot_chunk_cap && ps->slot[0].kw_off) return cudaSuccess;
+  free_slots(ps);
+  cudaError_t e = cudaSuccess;
+  for (genie_index& s : ps->slot) {
+    if (e == cudaSuccess) e = cudaMalloc(&s.kw_off, ((uint64_t)ps->vocab + 1) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&s.post_ids, post * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s.chunk_pos, chunk * 4);
+    s.device = ps->device;
+    s.vocab = ps->vocab;
+  }
+  if (e != cudaSuccess) {
+    free_slots(ps);
+    return e;
+  }
+  ps->slot_post_cap = post;
+  ps->slot_chunk_cap = chunk;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" genie_status genie_parts_create(genie_parts** out) {
+  if (!out) return fail(GENIE_ERR_INVALID_ARG, "genie_parts_create: out is NULL");
+  genie_parts* ps = new genie_parts();
+  cudaError_t e = cudaGetDevice(&ps->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ps->copy, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&ps->copied[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ps->used[i], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    genie_parts_destroy(ps);
+    return fail_cuda(e, "genie_parts_create");
+  }
+  *out = ps;
+  return GENIE_OK;
+}
+
+extern "C" void genie_parts_destroy(genie_parts* ps) {
+  if (!ps) return;
+  if (ps->copy) cudaStreamSynchronize(ps->copy);
+  cudaDeviceSynchronize();
+  for (HostPart& h : ps->parts) {
+    cudaFreeHost(h.kw_off);
+    cudaFreeHost(h.post_ids);
+    cudaFreeHost(h.chunk_pos);
+  }
+  free_slots(ps);
+  for (int i = 0; i < 2; ++i) {
+    if (ps->copied[i]) cudaEventDestroy(ps->copied[i]);
+    if (ps->used[i]) cudaEventDestroy(ps->used[i]);
+  }
+  if (ps->copy) cudaStreamDestroy(ps->copy);
+  delete ps;
+}
+
+extern "C" genie_status genie_parts_add(genie_parts* ps, const genie_index* index, uint32_t id_base,
+                                        genie_stream stream) {
+  if (!ps || !index) return fail(GENIE_ERR_INVALID_ARG, "genie_parts_add: NULL argument");
+  if (!ps->parts.empty() && index->vocab != ps->vocab)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_parts_add: the parts must share one vocabulary");
+  const HostPart* last = ps->parts.empty() ? nullptr : &ps->parts.back();
+  if (last && (uint64_t)id_base < (uint64_t)last->base + last->n_objects)
+    return fail(GENIE_ERR_INVALID_ARG,
+                "genie_parts_add: parts must come in ascending, disjoint object-id ranges");
+  if ((uint64_t)id_base + index->n_objects >= 0xFFFFFFFFull)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_parts_add: global object ids must stay below 2^32 - 1");
+  HostPart h;
+  h.base = id_base;
+  h.n_objects = index->n_objects;
+  h.max_object_len = index->max_object_len;
+  h.chunk_shift = index->chunk_shift;
+  h.n_chunks = index->n_chunks;
+  h.nnz = index->nnz;
+  h.post_len = ((index->nnz + 3) & ~3ull) + 4;  // the padded List Array
+  h.chunk_len = (uint64_t)index->vocab * (index->n_chunks + 1);
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e = cudaMallocHost(&h.kw_off, ((uint64_t)index->vocab + 1) * 8);
+  if (e == cudaSuccess) e = cudaMallocHost(&h.post_ids, h.post_len * 4);
+  if (e == cudaSuccess) e = cudaMallocHost(&h.chunk_pos, h.chunk_len * 4);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h.kw_off, index->kw_off, ((uint64_t)index->vocab + 1) * 8,
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h.post_ids, index->post_ids, h.post_len * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h.chunk_pos, index->chunk_pos, h.chunk_len * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFreeHost(h.kw_off);
+    cudaFreeHost(h.post_ids);
+    cudaFreeHost(h.chunk_pos);
+    return fail_cuda(e, "genie_parts_add");
+  }
+  ps->vocab = index->vocab;
+  ps->parts.push_back(h);
+  return GENIE_OK;
+}
+
+extern "C" genie_status genie_parts_get_info(const genie_parts* ps, genie_parts_info* out) {
+  if (!ps || !out) return fail(GENIE_ERR_INVALID_ARG, "genie_parts_get_info: NULL argument");
+  out->n_parts = (uint32_t)ps->parts.size();
+  out->vocab = ps->vocab;
+  out->n_objects = ps->parts.empty() ? 0 : ps->parts.back().base + ps->parts.back().n_objects;
+  out->host_bytes = 0;
+  out->max_part_bytes = 0;
+  for (const HostPart& h : ps->parts) {
+    const uint64_t b = ((uint64_t)ps->vocab + 1) * 8 + h.post_len * 4 + h.chunk_len * 4;
+    out->host_bytes += b;
+    out->max_part_bytes = std::max(out->max_part_bytes, b);
+  }
+  return GENIE_OK;
+}
+
+extern "C" genie_status genie_parts_search(genie_parts* ps, const uint32_t* d_q_off,
+                                           const uint32_t* d_q_kw, uint32_t n_queries, uint32_t k,
+                                           const uint32_t* d_k, uint32_t* d_ids, uint32_t* d_counts,
+                                           uint32_t* d_n_valid, genie_stream stream) {
+  if (!ps || !d_q_off || !d_ids || !d_counts || !d_n_valid)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_parts_search: NULL argument");
+  if (ps->parts.empty()) return fail(GENIE_ERR_INVALID_ARG, "genie_parts_search: no parts");
+  if (k == 0 || k > GENIE_MAX_K) return fail(GENIE_ERR_INVALID_ARG, "genie_parts_search: k must be in 1..GENIE_MAX_K");
+  if (n_queries == 0) return GENIE_OK;
+  cudaStream_t s = as_stream(stream);
+  const uint32_t P = (uint32_t)ps->parts.size(), Q = n_queries;
+  GENIE_CUDA_TRY(ensure_slots(ps));
+  // scratch: per-part outputs, then keys, bounds and part bases
+  const uint64_t out_words = (uint64_t)P * Q * k;
+  const uint64_t bytes = out_words * 8 + (uint64_t)P * Q * 4 + out_words * 8 + (uint64_t)Q * 4 + P * 4 + 64;
+  unsigned char* base = nullptr;
+  GENIE_CUDA_TRY(cudaMallocAsync((void**)&base, bytes, s));
+  uint32_t* p_ids = reinterpret_cast<uint32_t*>(base);
+  uint32_t* p_counts = p_ids + out_words;
+  uint32_t* p_nv = p_counts + out_words;
+  unsigned long long* keys =
+      reinterpret_cast<unsigned long long*>(((uintptr_t)(p_nv + (uint64_t)P * Q) + 15) & ~(uintptr_t)15);
+  uint32_t* max_b = reinterpret_cast<uint32_t*>(keys + out_words);
+  uint32_t* d_bases = max_b + Q;
+  std::vector<uint32_t> bases(P);
+  for (uint32_t p = 0; p < P; ++p) bases[p] = ps->parts[p].base;
+  cudaError_t e = cudaMemsetAsync(max_b, 0, (size_t)Q * 4, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_bases, bases.data(), P * 4, cudaMemcpyHostToDevice, s);
+  // the slots are free once the work enqueued so far on `s` is done
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventRecord(ps->used[i], s);
+  auto load = [&](uint32_t p) -> cudaError_t {
+    const HostPart& h = ps->parts[p];
+    genie_index& sl = ps->slot[p & 1];
+    cudaError_t r = cudaStreamWaitEvent(ps->copy, ps->used[p & 1], 0);
+    if (r == cudaSuccess)
+      r = cudaMemcpyAsync(sl.kw_off, h.kw_off, ((uint64_t)ps->vocab + 1) * 8, cudaMemcpyHostToDevice,
+                          ps->copy);
+    if (r == cudaSuccess)
+      r = cudaMemcpyAsync(sl.post_ids, h.post_ids, h.post_len * 4, cudaMemcpyHostToDevice, ps->copy);
+    if (r == cudaSuccess)
+      r = cudaMemcpyAsync(sl.chunk_pos, h.chunk_pos, h.chunk_len * 4, cudaMemcpyHostToDevice, ps->copy);
+    if (r == cudaSuccess) r = cudaEventRecord(ps->copied[p & 1], ps->copy);
+    return r;
+  };
+  genie_status st = GENIE_OK;
+  uint32_t za_len = 2;
+  if (e == cudaSuccess) e = load(0);
+  for (uint32_t p = 0; p < P && e == cudaSuccess && st == GENIE_OK; ++p) {
+    if (p + 1 < P) e = load(p + 1);  // overlaps the search of part p
+    if (e != cudaSuccess) break;
+    e = cudaStreamWaitEvent(s, ps->copied[p & 1], 0);
+    if (e != cudaSuccess) break;
+    const HostPart& h = ps->parts[p];
+    genie_index& sl = ps->slot[p & 1];
+    sl.n_objects = h.n_objects;
+    sl.nnz = h.nnz;
+    sl.max_object_len = h.max_object_len;
+    sl.chunk_shift = h.chunk_shift;
+    sl.n_chunks = h.n_chunks;
+    genie_queries* qs = nullptr;
+    st = genie_make_queries(&sl, d_q_off, d_q_kw, Q, stream, &qs);
+    if (st != GENIE_OK) break;
+    st = genie_search(&sl, qs, k, d_k, nullptr, p_ids + (uint64_t)p * Q * k,
+                      p_counts + (uint64_t)p * Q * k, p_nv + (uint64_t)p * Q, stream);
+    if (st == GENIE_OK) {
+      max_bound_kernel<<<grid_for(Q, 256), 256, 0, s>>>(qs->bound, Q, max_b);
+      za_len = std::max(za_len, qs->max_bound + 2);
+      e = cudaGetLastError();
+    }
+    genie_queries_destroy(qs);
+    if (e == cudaSuccess && st == GENIE_OK) e = cudaEventRecord(ps->used[p & 1], s);
+  }
+  if (e == cudaSuccess && st == GENIE_OK) {
+    part_keys_kernel<<<grid_for(out_words, 256), 256, 0, s>>>(p_ids, p_counts, p_nv, d_bases, P, Q,
+                                                               k, keys);
+    MergeArgs m;
+    m.cand = keys;
+    m.n_sel = Q;
+    m.q_sel = nullptr;
+    m.n_groups = P;
+    m.k = k;
+    m.k_arr = d_k;
+    m.bound = max_b;
+    m.za_len = za_len;
+    m.ids = d_ids;
+    m.counts = d_counts;
+    m.n_valid = d_n_valid;
+    const size_t msmem = dev::next_pow2(k) * 8 + (size_t)za_len * 4;
+    e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
+    if (e == cudaSuccess) {
+      merge_kernel<<<std::min<uint32_t>(Q, 152u * 16u), kMergeThreads, msmem, s>>>(m);
+      e = cudaGetLastError();
+    }
+  }
+  // the copy stream must not write a slot after this call returns
+  cudaError_t e2 = cudaStreamSynchronize(ps->copy);
+  cudaFreeAsync(base, s);
+  if (st != GENIE_OK) return st;
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return fail_cuda(e, "genie_parts_search");
+  return GENIE_OK;
+}

@@ -38,6 +38,8 @@ EXPORTED = (
     "genie_batch_create", "genie_batch_get_info", "genie_batch_destroy", "genie_batch_run",
     "genie_server_clock", "genie_server_create", "genie_server_destroy", "genie_server_submit",
     "genie_server_poll", "genie_server_get_stats", "genie_server_replay", "genie_calibrate",
+    "genie_parts_create", "genie_parts_destroy", "genie_parts_add", "genie_parts_get_info",
+    "genie_parts_search",
 )
 
 
@@ -45,6 +47,12 @@ class GenieError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__("genie status %d: %s" % (status, message))
         self.status = status
+
+
+class PartsInfo(ctypes.Structure):
+    _fields_ = [("n_parts", ctypes.c_uint32), ("vocab", ctypes.c_uint32),
+                ("n_objects", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("host_bytes", ctypes.c_uint64), ("max_part_bytes", ctypes.c_uint64)]
 
 
 class IndexInfo(ctypes.Structure):
@@ -173,6 +181,15 @@ def load(path: Optional[str] = None):
                                           ctypes.POINTER(u32)]
         lib.genie_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
         lib.genie_server_replay.argtypes = [vp, vp, vp, vp, vp, u32, u32, vp, vp, vp, vp]
+        lib.genie_parts_create.argtypes = [ctypes.POINTER(vp)]
+        lib.genie_parts_destroy.argtypes = [vp]
+        lib.genie_parts_destroy.restype = None
+        lib.genie_parts_add.argtypes = [vp, vp, u32, vp]
+        lib.genie_parts_get_info.argtypes = [vp, ctypes.POINTER(PartsInfo)]
+        lib.genie_parts_search.argtypes = [vp, vp, vp, u32, u32, vp, vp, vp, vp, vp]
+        for name in ("genie_parts_create", "genie_parts_add", "genie_parts_get_info",
+                     "genie_parts_search"):
+            getattr(lib, name).restype = st
         for name in ("genie_autotune", "genie_batch_create", "genie_batch_get_info",
                      "genie_batch_run", "genie_server_create", "genie_server_submit",
                      "genie_server_poll", "genie_server_get_stats", "genie_server_replay"):
@@ -398,6 +415,46 @@ def genie_autotune(index: Index, sample: Queries, k: int, cache_path: Optional[s
     _check(lib.genie_autotune(index.handle, sample.handle, k,
                               cache_path.encode() if cache_path else None, ctypes.byref(out)), lib)
     return out
+
+
+class Parts:
+    """Owning wrapper of a ``genie_parts*``: an index in parts held in pinned
+    host memory and searched part by part (multiple loadings)."""
+
+    def __init__(self):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.genie_parts_create(ctypes.byref(h)), lib)
+        self.handle = h.value
+
+    def add(self, index: "Index", id_base: int, stream=None) -> None:
+        lib = load()
+        _check(lib.genie_parts_add(self.handle, index.handle, id_base, _stream(stream)), lib)
+
+    @property
+    def info(self) -> PartsInfo:
+        lib = load()
+        out = PartsInfo()
+        _check(lib.genie_parts_get_info(self.handle, ctypes.byref(out)), lib)
+        return out
+
+    def search(self, d_q_off, d_q_kw, n_queries: int, k: int, d_ids, d_counts, d_n_valid,
+               d_k=None, stream=None) -> None:
+        lib = load()
+        _check(lib.genie_parts_search(self.handle, _ptr(d_q_off), _ptr(d_q_kw), n_queries, k,
+                                      _ptr(d_k), _ptr(d_ids), _ptr(d_counts), _ptr(d_n_valid),
+                                      _stream(stream)), lib)
+
+    def close(self):
+        if self.handle:
+            load().genie_parts_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

@@ -75,6 +75,36 @@ def search(index: genie.Index, queries: genie.Queries, k, opts: Optional[genie.S
     return out
 
 
+def build_parts(w, ranges, chunk_shift: int = 0, stream=None) -> genie.Parts:
+    """A part store over the ascending, disjoint object-id ranges
+    ``[(start, end), ...]`` of a keyword workload; each part is indexed with
+    local ids and placed at global id ``start``."""
+    parts = genie.Parts()
+    off = w.obj_off.astype(np.int64)
+    for a, b in ranges:
+        sub_off = (off[a:b + 1] - off[a]).astype(np.uint32)
+        sub_kw = w.obj_kw[off[a]:off[b]]
+        idx = genie.genie_build_index(to_dev(sub_off), to_dev(sub_kw), b - a, w.vocab, chunk_shift,
+                                      stream)
+        parts.add(idx, a, stream)
+        idx.close()
+    return parts
+
+
+def search_parts(parts: genie.Parts, w, k, out: Optional[Outputs] = None, stream=None) -> Outputs:
+    """genie_parts_search over a keyword workload's queries."""
+    if np.isscalar(k):
+        kmax, d_k = int(k), None
+    else:
+        karr = np.asarray(k, dtype=np.uint32)
+        kmax, d_k = int(karr.max()), to_dev(karr)
+    if out is None:
+        out = Outputs(w.n_queries, kmax)
+    parts.search(to_dev(w.q_off), to_dev(w.q_kw), w.n_queries, kmax, out.ids, out.counts,
+                 out.n_valid, d_k=d_k, stream=stream)
+    return out
+
+
 def query_facts(queries: genie.Queries) -> dict:
     n = queries.n_queries
     bound = torch.empty(n, dtype=torch.int32, device="cuda")

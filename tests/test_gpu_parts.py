@@ -1,0 +1,98 @@
+"""Multiple loadings (GPU): an index split into parts by object id, held in
+pinned host memory and searched part by part (Sec. 3.4), returns exactly the
+oracle's top-k of the whole object set; the part store checks its inputs."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_1603_08390_gb300 import _build, genie, runner
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    _build.build()
+    genie.load()
+
+
+def _check(res, ref):
+    for q in range(len(ref["n_valid"])):
+        n = int(ref["n_valid"][q])
+        assert res["n_valid"][q] == n, q
+        assert np.array_equal(res["ids"][q, :n], ref["ids"][q, :n]), q
+        assert np.array_equal(res["counts"][q, :n], ref["counts"][q, :n]), q
+        assert np.all(res["ids"][q, n:] == 0xFFFFFFFF)
+        assert np.all(res["counts"][q, n:] == 0)
+
+
+def test_uneven_parts_equal_one_index_and_the_oracle():
+    w = synth.sets(150_000, (16, 128), 1 << 16, 120, (8, 300), 10, config=50)
+    ranges = [(0, 61_000), (61_000, 118_500), (118_500, 150_000)]
+    parts = runner.build_parts(w, ranges, chunk_shift=13)
+    info = parts.info
+    assert info.n_parts == 3 and info.n_objects == w.n_objects and info.vocab == w.vocab
+    got = runner.search_parts(parts, w, 10).host()
+    torch.cuda.synchronize()
+    _check(got, oracle.topk(w))
+    idx = runner.build_index(w, 13)
+    whole = runner.search(idx, runner.compile_queries(idx, w), 10).host()
+    for key in got:
+        assert np.array_equal(got[key], whole[key]), key
+    # a second search reuses the device slots
+    again = runner.search_parts(parts, w, 10).host()
+    for key in got:
+        assert np.array_equal(got[key], again[key]), key
+    parts.close()
+
+
+def test_parts_with_an_id_gap_and_per_query_k():
+    w = synth.lsh(60_000, 40, 30, config=51)
+    rng = np.random.default_rng(3)
+    ks = rng.integers(1, 31, w.n_queries).astype(np.uint32)
+    # objects 20_000 .. 24_999 hold no keyword: they belong to no part
+    off = w.obj_off.astype(np.int64)
+    lens = np.diff(off)
+    lens[20_000:25_000] = 0
+    keep = np.ones(len(w.obj_kw), dtype=bool)
+    keep[off[20_000]:off[25_000]] = False
+    w.obj_kw = w.obj_kw[keep]
+    w.obj_off = np.concatenate([[0], np.cumsum(lens)]).astype(np.uint32)
+    parts = runner.build_parts(w, [(0, 20_000), (25_000, 60_000)], chunk_shift=12)
+    got = runner.search_parts(parts, w, ks).host()
+    torch.cuda.synchronize()
+    _check(got, oracle.topk(w, k=ks))
+    parts.close()
+
+
+def test_part_store_inputs_are_checked():
+    w = synth.sets(10_000, (4, 16), 500, 8, (2, 10), 5, config=52)
+    off = w.obj_off.astype(np.int64)
+    parts = genie.Parts()
+    with pytest.raises(genie.GenieError) as e:   # no part yet
+        runner.search_parts(parts, w, 5)
+    assert e.value.status == genie.GENIE_ERR_INVALID_ARG
+    a = genie.genie_build_index(runner.to_dev(w.obj_off), runner.to_dev(w.obj_kw), w.n_objects,
+                                w.vocab, 0, None)
+    parts.add(a, 0)
+    with pytest.raises(genie.GenieError) as e:   # overlapping id range
+        parts.add(a, w.n_objects - 1)
+    assert e.value.status == genie.GENIE_ERR_INVALID_ARG
+    b = genie.genie_build_index(runner.to_dev(w.obj_off), runner.to_dev(w.obj_kw), w.n_objects,
+                                w.vocab + 7, 0, None)
+    with pytest.raises(genie.GenieError) as e:   # another vocabulary
+        parts.add(b, w.n_objects)
+    assert e.value.status == genie.GENIE_ERR_INVALID_ARG
+    with pytest.raises(genie.GenieError) as e:   # ids past 2^32 - 2
+        parts.add(a, 0xFFFFFFFF - 5)
+    assert e.value.status == genie.GENIE_ERR_INVALID_ARG
+    got = runner.search_parts(parts, w, 5).host()   # the one valid part
+    torch.cuda.synchronize()
+    _check(got, oracle.topk(w))
+    for x in (a, b, parts):
+        x.close()
+    del off
