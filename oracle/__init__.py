@@ -15,6 +15,9 @@ Contents
   * ``counts``    -- the full count matrix for small cases.
   * ``cpq``       -- a serial replay of Algorithm 1 (pure Python, small cases).
   * ``mlp``       -- the k-th-count predictor network in float64 numpy.
+  * ``sa``        -- sequence search by ordered n-grams (Sec. 5.1): n-gram
+                     keywords, edit distance (C++, ``sa_oracle.cpp``), the
+                     verification of Algorithm 2 and the check of Theorem 5.2.
 
 Parity pins live in ``tests/test_oracle_*.py``.
 """
@@ -33,15 +36,17 @@ _LOCK = threading.Lock()
 
 
 def build(force: bool = False) -> str:
-    """Compile ``mc_oracle.cpp`` (g++ -O3, OpenMP) into ``oracle/_build``."""
+    """Compile ``mc_oracle.cpp`` and ``sa_oracle.cpp`` (g++ -O3, OpenMP) into
+    ``oracle/_build``."""
     out_dir = os.path.join(_HERE, "_build")
     so = os.path.join(out_dir, "liboracle.so")
-    src = os.path.join(_HERE, "mc_oracle.cpp")
-    if not force and os.path.exists(so) and os.path.getmtime(so) >= os.path.getmtime(src):
+    srcs = [os.path.join(_HERE, "mc_oracle.cpp"), os.path.join(_HERE, "sa_oracle.cpp")]
+    if (not force and os.path.exists(so)
+            and all(os.path.getmtime(so) >= os.path.getmtime(x) for x in srcs)):
         return so
     os.makedirs(out_dir, exist_ok=True)
     tmp = so + ".%d.tmp" % os.getpid()
-    subprocess.check_call(["g++", "-O3", "-fopenmp", "-shared", "-fPIC", "-o", tmp, src])
+    subprocess.check_call(["g++", "-O3", "-fopenmp", "-shared", "-fPIC", "-o", tmp] + srcs)
     os.replace(tmp, so)
     return so
 
@@ -65,6 +70,15 @@ def _lib():
             lib.cpuidx_topk_keywords.argtypes = [u32, p, p, u32, u32, p, p, p, u32, p, p, p,
                                                  p, p, i]
             lib.cpuidx_topk_keywords.restype = i
+            u64 = ctypes.c_uint64
+            lib.oracle_ed.argtypes = [p, u32, p, u32]
+            lib.oracle_ed.restype = u32
+            lib.oracle_ed_pairs.argtypes = [p, p, p, p, u64, p, p]
+            lib.oracle_ed_pairs.restype = i
+            lib.oracle_sa_grams.argtypes = [u32, p, p, u32, u32, u32, p, p]
+            lib.oracle_sa_grams.restype = i
+            lib.oracle_sa_topk_ed.argtypes = [u32, p, p, u32, p, p, u32, p, p]
+            lib.oracle_sa_topk_ed.restype = i
             _LIB = lib
     return _LIB
 

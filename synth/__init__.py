@@ -58,6 +58,8 @@ def _lib():
             lib.synth_permutation.argtypes = [u64, u32, p]
             lib.synth_permutation.restype = None
             lib.synth_zipf_sets.argtypes = [u64, u64, u32, dbl, p, p, p]
+            lib.synth_chars.argtypes = [u64, u64, u32, dbl, p, p]
+            lib.synth_chars.restype = None
             lib.synth_zipf_sets.restype = ctypes.c_int
             _LIB = lib
     return _LIB
@@ -266,3 +268,70 @@ def config(n: int) -> Workload:
         w.k = np.asarray([1, 10, 100], dtype=np.uint32)[rng.integers(0, 3, size=w.n_queries)]
         return w
     raise ValueError("config must be 1..5")
+
+
+@dataclass
+class Sequences:
+    """Data and query sequences over the alphabet 0 .. sigma-1, in CSR form
+    (``s_off[N+1]``, ``s_chars``; ``q_off[Q+1]``, ``q_chars``, uint8 chars).
+    ``q_src[q]`` is the data sequence query q was edited from and
+    ``q_edits[q]`` how many edits were applied."""
+    n_seqs: int
+    sigma: int
+    s_off: np.ndarray
+    s_chars: np.ndarray
+    n_queries: int
+    q_off: np.ndarray
+    q_chars: np.ndarray
+    q_src: np.ndarray
+    q_edits: np.ndarray
+
+    def subset(self, qids) -> "Sequences":
+        qids = np.asarray(qids)
+        qo = self.q_off.astype(np.int64)
+        parts = [self.q_chars[qo[q]:qo[q + 1]] for q in qids]
+        lens = np.array([len(p) for p in parts], np.int64)
+        off = np.concatenate([[0], np.cumsum(lens)]).astype(np.uint32)
+        chars = np.concatenate(parts).astype(np.uint8) if len(parts) else np.zeros(0, np.uint8)
+        return Sequences(self.n_seqs, self.sigma, self.s_off, self.s_chars, len(qids), off, chars,
+                         self.q_src[qids], self.q_edits[qids])
+
+
+def sequences(n_seqs: int = 1 << 20, length=(40, 100), sigma: int = 26, n_queries: int = 1024,
+              edits=(1, 6), config: int = 6, s: float = 1.0) -> Sequences:
+    """Strings for sequence search under edit distance (the DBLP-like case of
+    Sec. 5.1): lengths uniform in ``length``, characters drawn with Zipf(s)
+    frequencies over the alphabet; each query is a random data sequence with
+    a uniform number of random edits in ``edits`` (substitution, insertion or
+    deletion at a random position)."""
+    assert 2 <= sigma <= 256
+    rng_q = np.random.default_rng([SEED_BASE + config, ROLE_QUERIES])
+    w = 1.0 / np.arange(1, sigma + 1, dtype=np.float64) ** s
+    p = w / w.sum()
+    lens = np.empty(n_seqs, np.uint32)
+    _lib().synth_set_lengths(_seed(config, ROLE_OBJECTS), n_seqs, length[0], length[1],
+                             _ptr(lens))
+    off64 = np.concatenate([[0], np.cumsum(lens, dtype=np.uint64)]).astype(np.uint64)
+    s_chars = np.empty(max(int(off64[-1]), 1), np.uint8)
+    _lib().synth_chars(_seed(config, ROLE_OBJECTS), n_seqs, sigma, s, _ptr(off64), _ptr(s_chars))
+    s_chars = s_chars[:int(off64[-1])]
+    s_off = off64.astype(np.uint32)
+    q_src = rng_q.integers(0, n_seqs, n_queries).astype(np.uint32)
+    q_edits = rng_q.integers(edits[0], edits[1] + 1, n_queries).astype(np.uint32)
+    qs = []
+    for q in range(n_queries):
+        a = list(s_chars[s_off[q_src[q]]:s_off[q_src[q] + 1]])
+        for _ in range(int(q_edits[q])):
+            op = rng_q.integers(0, 3)
+            pos = int(rng_q.integers(0, len(a) + (1 if op == 1 else 0))) if a else 0
+            c = int(rng_q.choice(sigma, p=p))
+            if op == 0 and a:
+                a[pos] = c
+            elif op == 1 or not a:
+                a.insert(pos, c)
+            else:
+                del a[pos]
+        qs.append(np.array(a, np.uint8))
+    q_off = np.concatenate([[0], np.cumsum([len(x) for x in qs])]).astype(np.uint32)
+    q_chars = np.concatenate(qs).astype(np.uint8)
+    return Sequences(n_seqs, sigma, s_off, s_chars, n_queries, q_off, q_chars, q_src, q_edits)

@@ -170,3 +170,30 @@ int synth_zipf_sets(uint64_t seed, uint64_t n_sets, uint32_t vocab, double s,
   free(cdf);
   return bad ? 2 : 0;
 }
+
+/*
+ * Characters of sequences: sequence t holds off[t+1] - off[t] characters, each
+ * drawn independently from the alphabet 0 .. sigma-1 with probability
+ * proportional to (c+1)^-s (inverse transform over the cumulative weights).
+ */
+void synth_chars(uint64_t seed, uint64_t n_seqs, uint32_t sigma, double s, const uint64_t* off,
+                 uint8_t* out) {
+  double cdf[256];
+  double total = 0.0;
+  for (uint32_t c = 0; c < sigma && c < 256; ++c) {
+    total += pow((double)(c + 1), -s);
+    cdf[c] = total;
+  }
+#pragma omp parallel for schedule(static, 1024)
+  for (int64_t t = 0; t < (int64_t)n_seqs; ++t) {
+    for (uint64_t i = off[t]; i < off[t + 1]; ++i) {
+      const double u = unif(draw(seed, ST_KW, (uint64_t)t, i - off[t])) * total;
+      uint32_t lo = 0, hi = sigma - 1;
+      while (lo < hi) {  /* first c with cdf[c] > u */
+        const uint32_t mid = (lo + hi) >> 1;
+        if (cdf[mid] > u) hi = mid; else lo = mid + 1;
+      }
+      out[i] = (uint8_t)lo;
+    }
+  }
+}
