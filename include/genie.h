@@ -564,6 +564,66 @@ genie_status genie_parts_search(genie_parts* parts, const uint32_t* d_q_off, con
                                 uint32_t* d_ids, uint32_t* d_counts, uint32_t* d_n_valid,
                                 genie_stream stream);
 
+/* ------------------------------------------------------------------------ */
+/* Sequence search by ordered n-grams (Sec. 5.1, the shotgun-and-assembly    */
+/* scheme under edit distance)                                               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Ordered n-grams of sequences as keyword sets (Sec. 5.1.1).  The window
+ * S[p .. p+n-1] is read as the base-sigma number g (first character most
+ * significant); its occurrence number i counts the equal windows before it
+ * in S; the keyword is g * R + i (< sigma^n * R, the vocabulary to build the
+ * index with).
+ *   d_off [n_seqs+1], d_chars: sequences in CSR form (device), characters
+ *              0 .. sigma-1 (uint8).
+ *   n >= 1, sigma 2 .. 256, R >= 1, with sigma^n * R <= 2^31.
+ *   d_kw_off [n_seqs+1] (device, written): keyword offsets; sequence s has
+ *              max(0, len - n + 1) keywords, in window order.
+ *   d_kw       (device, written): the keywords; kw_capacity entries.
+ *   total      (host, written): the number of keywords.
+ * Synchronises `stream`.  Errors: INVALID_ARG (parameters, a character >=
+ * sigma, an n-gram occurring R or more times in one sequence), CAPACITY
+ * (kw_capacity < total; d_kw_off and *total are still written), CUDA.
+ */
+genie_status genie_sa_grams(const uint32_t* d_off, const uint8_t* d_chars, uint32_t n_seqs,
+                            uint32_t n, uint32_t sigma, uint32_t R, uint32_t* d_kw_off,
+                            uint32_t* d_kw, uint64_t kw_capacity, uint64_t* total,
+                            genie_stream stream);
+
+/*
+ * Verification of the K candidates of each query (Algorithm 2, Theorem 5.2).
+ *   d_q_off [n_queries+1], d_q_chars: query sequences (device); every query
+ *              at most max_query_len <= 512 characters.
+ *   d_s_off, d_s_chars: the data sequences (device).
+ *   d_cand_ids, d_cand_counts [n_queries * K], d_cand_n [n_queries]: the
+ *              output of genie_search (or genie_parts_search) with k = K over
+ *              the sequences' n-gram index: candidates in (count desc, id
+ *              asc) order.
+ *   n: the n-gram length of the index; 1 <= k <= K <= GENIE_MAX_K.
+ * Per query, in candidate order, the edit distance of a candidate is used
+ * until the n-gram bound of Theorem 5.1 rules out every later one (the
+ * filtering bound theta = |Q| - n + 1 - n (tau_k - 1), tau_k the k-th best
+ * distance so far, once k candidates were taken; Algorithm 2 is the case k =
+ * 1), candidates whose length differs from |Q| by more than tau_k being
+ * skipped.  Outputs:
+ *   d_ids, d_ed [n_queries * k]: the k best (distance asc, then candidate
+ *              order); unused slots 0xFFFFFFFF.
+ *   d_n_out [n_queries]: results written (min(k, candidates)).
+ *   d_certified [n_queries]: 1 when Theorem 5.2 shows these are the true top-k
+ *              under edit distance: the K-th candidate's count (0 with fewer
+ *              than K candidates) is below |Q| - n + 1 - tau_k * n.
+ *   d_examined [n_queries]: candidates whose distance the algorithm used.
+ * Enqueued on `stream`.  Errors: INVALID_ARG, CUDA.
+ */
+genie_status genie_sa_verify(const uint32_t* d_q_off, const uint8_t* d_q_chars, uint32_t n_queries,
+                             const uint32_t* d_s_off, const uint8_t* d_s_chars,
+                             const uint32_t* d_cand_ids, const uint32_t* d_cand_counts,
+                             const uint32_t* d_cand_n, uint32_t K, uint32_t k, uint32_t n,
+                             uint32_t max_query_len, uint32_t* d_ids, uint32_t* d_ed,
+                             uint32_t* d_n_out, uint32_t* d_certified, uint32_t* d_examined,
+                             genie_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,7 +39,7 @@ EXPORTED = (
     "genie_server_clock", "genie_server_create", "genie_server_destroy", "genie_server_submit",
     "genie_server_poll", "genie_server_get_stats", "genie_server_replay", "genie_calibrate",
     "genie_parts_create", "genie_parts_destroy", "genie_parts_add", "genie_parts_get_info",
-    "genie_parts_search",
+    "genie_parts_search", "genie_sa_grams", "genie_sa_verify",
 )
 
 
@@ -190,6 +190,12 @@ def load(path: Optional[str] = None):
         for name in ("genie_parts_create", "genie_parts_add", "genie_parts_get_info",
                      "genie_parts_search"):
             getattr(lib, name).restype = st
+        lib.genie_sa_grams.argtypes = [vp, vp, u32, u32, u32, u32, vp, vp, u64,
+                                       ctypes.POINTER(u64), vp]
+        lib.genie_sa_grams.restype = st
+        lib.genie_sa_verify.argtypes = [vp, vp, u32, vp, vp, vp, vp, vp, u32, u32, u32, u32,
+                                        vp, vp, vp, vp, vp, vp]
+        lib.genie_sa_verify.restype = st
         for name in ("genie_autotune", "genie_batch_create", "genie_batch_get_info",
                      "genie_batch_run", "genie_server_create", "genie_server_submit",
                      "genie_server_poll", "genie_server_get_stats", "genie_server_replay"):
@@ -415,6 +421,27 @@ def genie_autotune(index: Index, sample: Queries, k: int, cache_path: Optional[s
     _check(lib.genie_autotune(index.handle, sample.handle, k,
                               cache_path.encode() if cache_path else None, ctypes.byref(out)), lib)
     return out
+
+
+def genie_sa_grams(d_off, d_chars, n_seqs: int, n: int, sigma: int, R: int, d_kw_off, d_kw,
+                   kw_capacity: int, stream=None) -> int:
+    """Ordered n-gram keywords of sequences; returns the number written."""
+    lib = load()
+    total = ctypes.c_uint64()
+    _check(lib.genie_sa_grams(_ptr(d_off), _ptr(d_chars), n_seqs, n, sigma, R, _ptr(d_kw_off),
+                              _ptr(d_kw), kw_capacity, ctypes.byref(total), _stream(stream)), lib)
+    return int(total.value)
+
+
+def genie_sa_verify(d_q_off, d_q_chars, n_queries: int, d_s_off, d_s_chars, d_cand_ids,
+                    d_cand_counts, d_cand_n, K: int, k: int, n: int, max_query_len: int, d_ids,
+                    d_ed, d_n_out, d_certified, d_examined, stream=None) -> None:
+    lib = load()
+    _check(lib.genie_sa_verify(_ptr(d_q_off), _ptr(d_q_chars), n_queries, _ptr(d_s_off),
+                               _ptr(d_s_chars), _ptr(d_cand_ids), _ptr(d_cand_counts),
+                               _ptr(d_cand_n), K, k, n, max_query_len, _ptr(d_ids), _ptr(d_ed),
+                               _ptr(d_n_out), _ptr(d_certified), _ptr(d_examined),
+                               _stream(stream)), lib)
 
 
 class Parts:

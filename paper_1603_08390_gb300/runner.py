@@ -105,6 +105,67 @@ def search_parts(parts: genie.Parts, w, k, out: Optional[Outputs] = None, stream
     return out
 
 
+class SeqIndex:
+    """Device copies of data sequences and the index of their ordered n-grams."""
+
+    def __init__(self, s_off: np.ndarray, s_chars: np.ndarray, n: int, sigma: int, R: int,
+                 chunk_shift: int = 0, stream=None):
+        self.n, self.sigma, self.R = n, sigma, R
+        self.vocab = sigma ** n * R
+        self.n_seqs = len(s_off) - 1
+        self.d_off, self.d_chars = to_dev(s_off), to_dev(s_chars)
+        d_kw_off, d_kw, _ = sa_grams(self.d_off, self.d_chars, s_off, n, sigma, R, stream)
+        self.index = genie.genie_build_index(d_kw_off, d_kw, self.n_seqs, self.vocab, chunk_shift,
+                                             stream)
+
+
+def sa_grams(d_off, d_chars, off: np.ndarray, n: int, sigma: int, R: int, stream=None):
+    """Ordered n-gram keyword CSR (device) of sequences already on the device."""
+    lens = np.diff(off.astype(np.int64))
+    cap = max(int(np.maximum(lens - n + 1, 0).sum()), 1)
+    d_kw_off = torch.empty(len(off), dtype=torch.int32, device="cuda")
+    d_kw = torch.empty(cap, dtype=torch.int32, device="cuda")
+    total = genie.genie_sa_grams(d_off, d_chars, len(off) - 1, n, sigma, R, d_kw_off, d_kw, cap,
+                                 stream)
+    return d_kw_off, d_kw, total
+
+
+class SeqOutputs:
+    """Device results of a sequence search: K candidates and the k verified."""
+
+    def __init__(self, n_queries: int, K: int, k: int):
+        self.K, self.k = K, k
+        self.cand = Outputs(n_queries, K)
+        z = lambda m: torch.empty(m, dtype=torch.int32, device="cuda")
+        self.ids, self.ed = z(n_queries * k), z(n_queries * k)
+        self.n_out, self.certified, self.examined = z(n_queries), z(n_queries), z(n_queries)
+
+    def host(self) -> dict:
+        n = self.n_out.numel()
+        return {"ids": u32(self.ids).reshape(n, self.k), "ed": u32(self.ed).reshape(n, self.k),
+                "n_out": u32(self.n_out), "certified": u32(self.certified).astype(bool),
+                "examined": u32(self.examined), "candidates": self.cand.host()}
+
+
+def sa_search(si: SeqIndex, q_off: np.ndarray, q_chars: np.ndarray, K: int, k: int,
+              out: Optional[SeqOutputs] = None, stream=None, d_q=None) -> SeqOutputs:
+    """Shotgun and assembly (Sec. 5.1): the queries' ordered n-grams, the top-K
+    sequences by match count, then the verification of the candidates."""
+    d_q_off, d_q_chars = d_q if d_q is not None else (to_dev(q_off), to_dev(q_chars))
+    n_q = len(q_off) - 1
+    if out is None:
+        out = SeqOutputs(n_q, K, k)
+    qk_off, qk, _ = sa_grams(d_q_off, d_q_chars, q_off, si.n, si.sigma, si.R, stream)
+    qs = genie.genie_make_queries(si.index, qk_off, qk, n_q, stream)
+    genie.genie_search(si.index, qs, K, out.cand.ids, out.cand.counts, out.cand.n_valid,
+                       stream=stream)
+    max_len = int(np.diff(q_off.astype(np.int64)).max()) if n_q else 0
+    genie.genie_sa_verify(d_q_off, d_q_chars, n_q, si.d_off, si.d_chars, out.cand.ids,
+                          out.cand.counts, out.cand.n_valid, K, k, si.n, max_len, out.ids, out.ed,
+                          out.n_out, out.certified, out.examined, stream)
+    return out
+
+
 def query_facts(queries: genie.Queries) -> dict:
     n = queries.n_queries
     bound = torch.empty(n, dtype=torch.int32, device="cuda")
