@@ -15,6 +15,8 @@ Contents
   * ``counts``    -- the full count matrix for small cases.
   * ``cpq``       -- a serial replay of Algorithm 1 (pure Python, small cases).
   * ``mlp``       -- the k-th-count predictor network in float64 numpy.
+  * ``lsh``       -- LSH keywords of points (Sec. 4.1): p-stable hashing and
+                     random binning with its re-hash (C++, ``lsh_oracle.cpp``).
   * ``sa``        -- sequence search by ordered n-grams (Sec. 5.1): n-gram
                      keywords, edit distance (C++, ``sa_oracle.cpp``), the
                      verification of Algorithm 2 and the check of Theorem 5.2.
@@ -36,17 +38,18 @@ _LOCK = threading.Lock()
 
 
 def build(force: bool = False) -> str:
-    """Compile ``mc_oracle.cpp`` and ``sa_oracle.cpp`` (g++ -O3, OpenMP) into
-    ``oracle/_build``."""
+    """Compile ``mc_oracle.cpp``, ``sa_oracle.cpp`` and ``lsh_oracle.cpp``
+    (g++ -O3, OpenMP, no floating-point contraction) into ``oracle/_build``."""
     out_dir = os.path.join(_HERE, "_build")
     so = os.path.join(out_dir, "liboracle.so")
-    srcs = [os.path.join(_HERE, "mc_oracle.cpp"), os.path.join(_HERE, "sa_oracle.cpp")]
+    srcs = [os.path.join(_HERE, x) for x in ("mc_oracle.cpp", "sa_oracle.cpp", "lsh_oracle.cpp")]
     if (not force and os.path.exists(so)
             and all(os.path.getmtime(so) >= os.path.getmtime(x) for x in srcs)):
         return so
     os.makedirs(out_dir, exist_ok=True)
     tmp = so + ".%d.tmp" % os.getpid()
-    subprocess.check_call(["g++", "-O3", "-fopenmp", "-shared", "-fPIC", "-o", tmp] + srcs)
+    subprocess.check_call(["g++", "-O3", "-fopenmp", "-ffp-contract=off", "-shared", "-fPIC",
+                           "-o", tmp] + srcs)
     os.replace(tmp, so)
     return so
 
@@ -79,6 +82,11 @@ def _lib():
             lib.oracle_sa_grams.restype = i
             lib.oracle_sa_topk_ed.argtypes = [u32, p, p, u32, p, p, u32, p, p]
             lib.oracle_sa_topk_ed.restype = i
+            f32 = ctypes.c_float
+            lib.oracle_lsh_pstable.argtypes = [u64, u32, p, u32, p, p, f32, u32, p]
+            lib.oracle_lsh_pstable.restype = i
+            lib.oracle_lsh_rbh.argtypes = [u64, u32, p, u32, p, p, p, u32, p]
+            lib.oracle_lsh_rbh.restype = i
             _LIB = lib
     return _LIB
 

@@ -335,3 +335,20 @@ def sequences(n_seqs: int = 1 << 20, length=(40, 100), sigma: int = 26, n_querie
     q_off = np.concatenate([[0], np.cumsum([len(x) for x in qs])]).astype(np.uint32)
     q_chars = np.concatenate(qs).astype(np.uint8)
     return Sequences(n_seqs, sigma, s_off, s_chars, n_queries, q_off, q_chars, q_src, q_edits)
+
+
+def lsh_params(family: str, dim: int, n_hash: int, scale: float, config: int = 7):
+    """Random draws of the LSH functions, passed to both the CUDA path and the
+    oracle.  family "pstable": a_i ~ N(0, I) (n_hash x dim), b_i ~ U[0, scale)
+    with scale = the bucket width w.  family "rbh": grid cell sizes
+    g_i[d] ~ Gamma(2, scale) with scale = the Laplacian kernel width sigma,
+    shifts u_i[d] ~ U[0, g_i[d]), and 32-bit re-hash keys."""
+    rng = np.random.default_rng([SEED_BASE + config, 11, 0 if family == "pstable" else 1])
+    if family == "pstable":
+        a = rng.standard_normal((n_hash, dim)).astype(np.float32)
+        b = (rng.random(n_hash) * scale).astype(np.float32)
+        return {"a": a, "b": b, "w": np.float32(scale)}
+    g = np.maximum(rng.gamma(2.0, scale, (n_hash, dim)), 1e-6).astype(np.float32)
+    u = (rng.random((n_hash, dim)) * g).astype(np.float32)
+    key = rng.integers(0, 1 << 32, n_hash, dtype=np.uint64).astype(np.uint32)
+    return {"g": g, "u": u, "key": key}
