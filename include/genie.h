@@ -624,6 +624,43 @@ genie_status genie_sa_verify(const uint32_t* d_q_off, const uint8_t* d_q_chars, 
                              uint32_t* d_n_out, uint32_t* d_certified, uint32_t* d_examined,
                              genie_stream stream);
 
+/* ------------------------------------------------------------------------ */
+/* LSH keywords of points (Sec. 4.1): a point becomes an object of m keywords */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Hash function i of m maps point p to keyword i * D + bucket (Sec. 4.1.2,
+ * O = [r_1(h_1(p)), ..., r_m(h_m(p))]); m * D <= 2^32.  Points are float32
+ * rows d_points[n_points][dim] (device); the output is d_kw[n_points][m]
+ * (device), which is the object CSR of genie_build_index with offsets
+ * o * m (and the query CSR of genie_make_queries).  Every floating-point step
+ * is one correctly rounded binary32 operation in the order given, so the
+ * keywords do not depend on the launch.  The random draws are inputs (device)
+ * and stay owned by the caller.  Enqueued on `stream`.  Errors: INVALID_ARG
+ * (NULL, zero sizes, m * D > 2^32, w <= 0), CUDA.
+ *
+ * p-stable hashing (Eqn. (plsh)): d_a[m][dim] (a_i, Gaussian for l2), d_b[m]
+ * (b_i in [0, w)), bucket width w:
+ *   s = fma(a_i[dim-1], p[dim-1], ... fma(a_i[1], p[1], fma(a_i[0], p[0], 0)))
+ *   bucket = floor((s + b_i) / w) mod D      (non-negative residue)
+ */
+genie_status genie_lsh_pstable(const float* d_points, uint64_t n_points, uint32_t dim,
+                               const float* d_a, const float* d_b, uint32_t m, float w, uint32_t D,
+                               uint32_t* d_kw, genie_stream stream);
+
+/*
+ * Random binning for the Laplacian kernel (the case study of Sec. 4.1.3):
+ * d_g[m][dim] grid cell sizes (Gamma(2, sigma) for kernel width sigma),
+ * d_u[m][dim] shifts in [0, g), d_key[m] re-hash keys:
+ *   c_d = floor((p[d] - u_i[d]) / g_i[d])      (saturated to int32)
+ *   x = key_i; for d = 0 .. dim-1: x = mix(x ^ c_d); bucket = mix(x) mod D,
+ * mix = the 32-bit finalizer lowbias32 (hash-prospector): x ^= x >> 16;
+ * x *= 0x7feb352d; x ^= x >> 15; x *= 0x846ca68b; x ^= x >> 16.
+ */
+genie_status genie_lsh_rbh(const float* d_points, uint64_t n_points, uint32_t dim,
+                           const float* d_g, const float* d_u, const uint32_t* d_key, uint32_t m,
+                           uint32_t D, uint32_t* d_kw, genie_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,7 +39,8 @@ EXPORTED = (
     "genie_server_clock", "genie_server_create", "genie_server_destroy", "genie_server_submit",
     "genie_server_poll", "genie_server_get_stats", "genie_server_replay", "genie_calibrate",
     "genie_parts_create", "genie_parts_destroy", "genie_parts_add", "genie_parts_get_info",
-    "genie_parts_search", "genie_sa_grams", "genie_sa_verify",
+    "genie_parts_search", "genie_sa_grams", "genie_sa_verify", "genie_lsh_pstable",
+    "genie_lsh_rbh",
 )
 
 
@@ -196,6 +197,10 @@ def load(path: Optional[str] = None):
         lib.genie_sa_verify.argtypes = [vp, vp, u32, vp, vp, vp, vp, vp, u32, u32, u32, u32,
                                         vp, vp, vp, vp, vp, vp]
         lib.genie_sa_verify.restype = st
+        lib.genie_lsh_pstable.argtypes = [vp, u64, u32, vp, vp, u32, f32, u32, vp, vp]
+        lib.genie_lsh_pstable.restype = st
+        lib.genie_lsh_rbh.argtypes = [vp, u64, u32, vp, vp, vp, u32, u32, vp, vp]
+        lib.genie_lsh_rbh.restype = st
         for name in ("genie_autotune", "genie_batch_create", "genie_batch_get_info",
                      "genie_batch_run", "genie_server_create", "genie_server_submit",
                      "genie_server_poll", "genie_server_get_stats", "genie_server_replay"):
@@ -421,6 +426,20 @@ def genie_autotune(index: Index, sample: Queries, k: int, cache_path: Optional[s
     _check(lib.genie_autotune(index.handle, sample.handle, k,
                               cache_path.encode() if cache_path else None, ctypes.byref(out)), lib)
     return out
+
+
+def genie_lsh_pstable(d_points, n_points: int, dim: int, d_a, d_b, m: int, w: float, D: int,
+                      d_kw, stream=None) -> None:
+    lib = load()
+    _check(lib.genie_lsh_pstable(_ptr(d_points), n_points, dim, _ptr(d_a), _ptr(d_b), m, w, D,
+                                 _ptr(d_kw), _stream(stream)), lib)
+
+
+def genie_lsh_rbh(d_points, n_points: int, dim: int, d_g, d_u, d_key, m: int, D: int, d_kw,
+                  stream=None) -> None:
+    lib = load()
+    _check(lib.genie_lsh_rbh(_ptr(d_points), n_points, dim, _ptr(d_g), _ptr(d_u), _ptr(d_key), m,
+                             D, _ptr(d_kw), _stream(stream)), lib)
 
 
 def genie_sa_grams(d_off, d_chars, n_seqs: int, n: int, sigma: int, R: int, d_kw_off, d_kw,
