@@ -160,11 +160,16 @@ KERNEL_SOURCES = ("cpq_device.cuh", "device_util.cuh", "search.cu")
 
 
 def kernel_source_sha() -> str:
-    """sha256 of the scan kernel's sources, concatenated in KERNEL_SOURCES order."""
+    """sha256 of the scan kernel's code: the KERNEL_SOURCES concatenated in
+    order, with comments removed and every run of blank space made one space
+    (so that a comment edit does not retire the profile)."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1603_08390_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1603_08390_gb300", "csrc", name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()
 
 

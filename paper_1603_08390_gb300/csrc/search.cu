@@ -36,9 +36,16 @@
 //    Bitmap Counter, so the result never depends on the hash table's luck.
 //  * Ties at the k-th count are filled in ascending object id from the
 //    Bitmap Counter (the paper breaks them randomly).
-//  * Gate passes of one warp that reach the same level share one
-//    ZipperArray atomic (warp match), which keeps the early levels, where
-//    thousands of objects pass at once, from serialising on one counter.
+//  * A warp counts a tile of postings, then tests the tile once (does any
+//    lane's largest new count reach AT?) and runs the Gate only for the
+//    slots that pass, one ZipperArray add per pass; the pass that fills a
+//    level to k advances AT.
+//  * AT seeds: a range that finishes adds the counts it reports to its
+//    query's histogram and publishes the k-th largest of them, a lower bound
+//    of the query's k-th count; later ranges start their AT there, and ties
+//    below the seed are left out (they cannot reach the query's top-k).  A
+//    range that starts with no seed selects its k-th count from the Bitmap
+//    Counter after counting instead of running the Gate from AT = 1.
 #include <algorithm>
 #include <cstdio>
 #include <mutex>
