@@ -74,32 +74,38 @@ __device__ __forceinline__ uint32_t vld(const uint32_t* p) { return *(const vola
 // multiple of the lanes per word, so the word of object id is
 // byte_off(id) - byte_off(range start) bytes into the range's counters, and
 // the lane inside the word is the low bits of the id.  inc: the word-sized
-// increment of that lane; get: the lane's value in a counter word.
+// increment of that lane; sel: a selector for the lane, pick: the lane's value
+// in a counter word given its selector (0 for a zero word whatever the
+// selector).  kHigh: the top bit of every lane; kOnes: 1 in every lane.
 template <int LOG2W>
 struct Lane;
 template <>
 struct Lane<4> {  // 16-bit counters, two per word
+  static constexpr uint32_t kHigh = 0x80008000u, kOnes = 0x00010001u;
   static __device__ __forceinline__ uint32_t byte_off(uint32_t id) { return (id & ~1u) << 1; }
   static __device__ __forceinline__ uint32_t inc(uint32_t id) { return (id & 1u) * 0xFFFFu + 1u; }
-  static __device__ __forceinline__ uint32_t get(uint32_t w, uint32_t id) {
-    return __byte_perm(w, 0u, 0x4410u + (id & 1u) * 0x22u);  // bytes 2l, 2l+1, then zeros
+  static __device__ __forceinline__ uint32_t sel(uint32_t id) { return 0x4410u + (id & 1u) * 0x22u; }
+  static __device__ __forceinline__ uint32_t pick(uint32_t w, uint32_t s) {
+    return __byte_perm(w, 0u, s);  // bytes 2l, 2l+1, then zeros
   }
 };
 template <>
 struct Lane<3> {  // 8-bit counters, four per word
+  static constexpr uint32_t kHigh = 0x80808080u, kOnes = 0x01010101u;
   static __device__ __forceinline__ uint32_t byte_off(uint32_t id) { return id & ~3u; }
   static __device__ __forceinline__ uint32_t inc(uint32_t id) { return 1u << ((id & 3u) << 3); }
-  static __device__ __forceinline__ uint32_t get(uint32_t w, uint32_t id) {
-    return __byte_perm(w, 0u, 0x4440u | (id & 3u));  // byte l, then zeros
+  static __device__ __forceinline__ uint32_t sel(uint32_t id) { return 0x4440u | (id & 3u); }
+  static __device__ __forceinline__ uint32_t pick(uint32_t w, uint32_t s) {
+    return __byte_perm(w, 0u, s);  // byte l, then zeros
   }
 };
 template <>
 struct Lane<2> {  // 4-bit counters, eight per word
+  static constexpr uint32_t kHigh = 0x88888888u, kOnes = 0x11111111u;
   static __device__ __forceinline__ uint32_t byte_off(uint32_t id) { return (id >> 1) & ~3u; }
   static __device__ __forceinline__ uint32_t inc(uint32_t id) { return 1u << ((id & 7u) << 2); }
-  static __device__ __forceinline__ uint32_t get(uint32_t w, uint32_t id) {
-    return (w >> ((id & 7u) << 2)) & 0xFu;
-  }
+  static __device__ __forceinline__ uint32_t sel(uint32_t id) { return (id & 7u) << 2; }
+  static __device__ __forceinline__ uint32_t pick(uint32_t w, uint32_t s) { return (w >> s) & 0xFu; }
 };
 
 // atomicAdd on a 32-bit shared-memory address, returning the old word
@@ -109,14 +115,15 @@ __device__ __forceinline__ uint32_t atom_add_shared(uint32_t saddr, uint32_t v) 
   return old;
 }
 
-// The same, done only where p != 0 (predicated; the address is not touched
-// otherwise); returns 0 where p == 0.
-__device__ __forceinline__ uint32_t atom_add_shared_if(uint32_t p, uint32_t saddr, uint32_t v) {
+// The same, done only where slot < len (unsigned; the address is not touched
+// otherwise); returns 0 where it is not done.
+__device__ __forceinline__ uint32_t atom_add_shared_in(uint32_t slot, uint32_t len, uint32_t saddr,
+                                                       uint32_t v) {
   uint32_t old = 0;
   asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q atom.shared.add.u32 %0, [%1], %2;\n\t}"
+      "{\n\t.reg .pred q;\n\tsetp.lt.u32 q, %1, %2;\n\t@q atom.shared.add.u32 %0, [%3], %4;\n\t}"
       : "+r"(old)
-      : "r"(saddr), "r"(v), "r"(p)
+      : "r"(slot), "r"(len), "r"(saddr), "r"(v)
       : "memory");
   return old;
 }
@@ -392,6 +399,8 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   }
   __syncthreads();
   const bool gateless = S.gateless;
+  // every count of the range stays below the top bit of its lane
+  const bool swar = B < (1u << ((1u << LOG2W) - 1));
 
   uint32_t n_gate = 0, n_ins = 0;
 
@@ -427,8 +436,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     // inside a run, by 32 segments per warp-wide step when it jumps to the
     // warp's next run.
     uint32_t j = 0;
-    auto locate_load = [&](uint32_t tt, uint32_t& lo_, uint32_t& hi_, uint32_t& st_,
-                           uint4 (&vv)[U]) {
+    auto locate = [&](uint32_t tt, uint32_t& lo_, uint32_t& hi_) -> uint32_t {
       if (tile_pre[j + 1] <= tt) {
         for (;;) {
           const uint32_t ball = __ballot_sync(0xFFFFFFFFu, tile_pre[j + 1 + lane] <= tt);
@@ -439,105 +447,127 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
       const uint2 sg = seg[j];
       lo_ = sg.x;
       hi_ = sg.y;
-      st_ = (lo_ & ~3u) + (tt - tile_pre[j]) * kTile;
+      return (lo_ & ~3u) + (tt - tile_pre[j]) * kTile;
+    };
+    // the tile's 16-byte vectors that start before hi_; the others keep what
+    // they held (their slots lie outside the list and are never counted)
+    auto load = [&](uint32_t st_, uint32_t hi_, uint4 (&vv)[U]) {
 #pragma unroll
       for (uint32_t u = 0; u < kUnroll; ++u) {
         const uint32_t idx = st_ + (u * 32 + lane) * 4;
-        vv[u] = idx < hi_ ? __ldg(reinterpret_cast<const uint4*>(A.post_ids + idx))
-                          : make_uint4(0, 0, 0, 0);
+        if (idx < hi_) vv[u] = __ldg(reinterpret_cast<const uint4*>(A.post_ids + idx));
       }
     };
-    // With two loads per lane the next tile is located and loaded while this
-    // one's counter updates are in flight (more registers would spill with
-    // four).
-    constexpr bool kPrefetch = U == 2;
+    // One id buffer: the counter updates of a tile take its ids, then the
+    // next tile is located and loaded into the same registers while the
+    // updates are in flight.  The Gate test needs the counts only, not the
+    // ids; the rare tile that passes it reloads its ids (from L1).
     uint32_t run = warp, t = run * kRun, t_end = min(t + kRun, total_tiles);
     uint32_t lo = 0, hi = 0, start = 0;
     uint4 v[kUnroll];
-    if (kPrefetch && t < total_tiles) locate_load(t, lo, hi, start, v);
+#pragma unroll
+    for (uint32_t u = 0; u < kUnroll; ++u) v[u] = make_uint4(0, 0, 0, 0);
+    if (t < total_tiles) {
+      start = locate(t, lo, hi);
+      load(start, hi, v);
+    }
     while (t < total_tiles) {
       // the tile after t: the next of this run, else the first of the warp's next run
       const bool run_ends = t + 1 >= t_end;
       const uint32_t tn = run_ends ? (run + nwarps) * kRun : t + 1;
       const uint32_t tn_end = run_ends ? min(tn + kRun, total_tiles) : t_end;
-      uint32_t lo1 = 0, hi1 = 0, start1 = 0;
-      uint4 v1[kUnroll];
-      if (!kPrefetch) locate_load(t, lo, hi, start, v);
-      // slots inside the list: four bits per 16-byte vector
-      uint32_t okm = 0xFFFFFFFFu;
-      if (start < lo || start + kTile > hi) {
-        okm = 0;
-#pragma unroll
-        for (uint32_t u = 0; u < kUnroll; ++u) {
-          const int p = (int)(start + (u * 32 + lane) * 4 - lo);  // >= -3
-          const int hc = min(max((int)(hi - lo) - p, 0), 4);
-          okm |= ((0xFu >> (4 - hc)) & (0xFu << (p < 0 ? -p : 0))) << (4 * u);
-        }
-      }
       // Bitmap Counter: one sub-word atomic add per posting (Algorithm 1,
-      // lines 1-2); val = the object's count before the add (0 for slots
+      // lines 1-2); val = the counter word before the add (0 for slots
       // outside the list).  Every id of a sublist lies in this block's range.
       uint32_t val[4 * kUnroll];
-      if (okm == 0xFFFFFFFFu) {
+      if (start >= lo && start + kTile <= hi) {
 #pragma unroll
         for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
           const uint32_t u = i >> 2, e = i & 3;
           const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
           val[i] = atom_add_shared(bc_adj + Lane<LOG2W>::byte_off(id), Lane<LOG2W>::inc(id));
         }
-      } else {
+      } else {  // a tile at either end of its list: slot positions checked one by one
+        const uint32_t d0 = start + lane * 4 - lo, len = hi - lo;
 #pragma unroll
         for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
           const uint32_t u = i >> 2, e = i & 3;
           const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-          val[i] = atom_add_shared_if(okm & (1u << i), bc_adj + Lane<LOG2W>::byte_off(id),
+          val[i] = atom_add_shared_in(d0 + u * 128 + e, len, bc_adj + Lane<LOG2W>::byte_off(id),
                                       Lane<LOG2W>::inc(id));
         }
       }
-      if (kPrefetch) {
-#pragma unroll
-        for (uint32_t u = 0; u < kUnroll; ++u) v1[u] = make_uint4(0, 0, 0, 0);
-        if (tn < total_tiles) locate_load(tn, lo1, hi1, start1, v1);
-      }
-      uint32_t vmax = 0;
-#pragma unroll
-      for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
-        const uint32_t u = i >> 2, e = i & 3;
-        const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-        val[i] = Lane<LOG2W>::get(val[i], id);
-        vmax = max(vmax, val[i]);
-      }
-      // Gate (Algorithm 1, lines 3-7) for the postings whose new count val + 1
-      // reaches the (possibly stale) AuditThreshold: rare, so a tile is tested
-      // once on each lane's largest count.
-      const uint32_t at_c = gateless ? 0xFFFFFFFFu : vld(&s_at);
-      if (__any_sync(0xFFFFFFFFu, vmax + 1 >= at_c)) {
-        uint32_t pm = 0;  // this lane's passing slots
-#pragma unroll
-        for (uint32_t i = 0; i < 4 * kUnroll; ++i) pm |= (uint32_t)(val[i] + 1 >= at_c) << i;
-        pm &= okm;
-        const uint32_t wm = __reduce_or_sync(0xFFFFFFFFu, pm);
+      // Gate (Algorithm 1, lines 3-7) for the postings whose new count reaches
+      // the (possibly stale) AuditThreshold: rare, so a tile is tested once.
+      // With headroom (every count below the lanes' top bit) the test runs
+      // on whole words: adding 2^(W-1) - (AT - 1) to every lane sets a lane's
+      // top bit exactly when the lane holds AT - 1 or more, without carries
+      // between lanes.  It also looks at the other lanes of each word: a
+      // false alarm costs only the exact test below.  Without headroom each
+      // posting's own lane is taken, before the ids are overwritten.
+      uint32_t at_c = 0;
+      bool hit = false;
+      if (!gateless && !swar) {
+        at_c = vld(&s_at);
+        uint32_t vmax = 0;
 #pragma unroll
         for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
-          if ((wm >> i) & 1u) {  // some lane passes at slot i
-            const uint32_t u = i >> 2, e = i & 3;
-            const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-            if ((pm >> i) & 1u)
-              gate_pass<LOG2W>(gs, id, val[i] + 1, kq, B, obj_base, ht_mask, ht_bits, n_gate,
-                               n_ins);
+          const uint32_t u = i >> 2, e = i & 3;
+          const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
+          vmax = max(vmax, Lane<LOG2W>::pick(val[i], Lane<LOG2W>::sel(id)));
+        }
+        hit = vmax + 1 >= at_c;
+      }
+      const uint32_t c_lo = lo, c_hi = hi, c_start = start;
+      if (tn < total_tiles) {
+        if (!run_ends && start + kTile < hi) start += kTile;  // same segment
+        else start = locate(tn, lo, hi);
+        load(start, hi, v);
+      }
+      if (!gateless) {
+        if (swar) {
+          at_c = vld(&s_at);
+          const uint32_t add = Lane<LOG2W>::kHigh - (at_c - 1) * Lane<LOG2W>::kOnes;
+          uint32_t acc = 0;
+#pragma unroll
+          for (uint32_t i = 0; i < 4 * kUnroll; ++i) acc |= val[i] + add;
+          hit = (acc & Lane<LOG2W>::kHigh) != 0;
+        }
+        if (__any_sync(0xFFFFFFFFu, hit)) {
+          // the exact test: each slot's own lane, inside the list
+          const uint32_t d0 = c_start + lane * 4 - c_lo, len = c_hi - c_lo;
+          uint32_t pm = 0;  // this lane's passing slots
+#pragma unroll
+          for (uint32_t u = 0; u < kUnroll; ++u) {
+            const uint32_t idx = c_start + (u * 32 + lane) * 4;
+            const uint4 w = idx < c_hi ? __ldg(reinterpret_cast<const uint4*>(A.post_ids + idx))
+                                       : make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (uint32_t e = 0; e < 4; ++e) {
+              const uint32_t i = u * 4 + e;
+              const uint32_t id = e == 0 ? w.x : e == 1 ? w.y : e == 2 ? w.z : w.w;
+              pm |= (uint32_t)(d0 + u * 128 + e < len &&
+                               Lane<LOG2W>::pick(val[i], Lane<LOG2W>::sel(id)) + 1 >= at_c)
+                    << i;
+            }
+          }
+          const uint32_t wm = __reduce_or_sync(0xFFFFFFFFu, pm);
+#pragma unroll
+          for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
+            if ((wm >> i) & 1u) {  // some lane passes at slot i
+              const uint32_t u = i >> 2, e = i & 3;
+              if ((pm >> i) & 1u) {
+                const uint32_t id = __ldg(A.post_ids + c_start + (u * 32 + lane) * 4 + e);
+                gate_pass<LOG2W>(gs, id, Lane<LOG2W>::pick(val[i], Lane<LOG2W>::sel(id)) + 1, kq,
+                                 B, obj_base, ht_mask, ht_bits, n_gate, n_ins);
+              }
+            }
           }
         }
       }
       if (run_ends) run += nwarps;
       t = tn;
       t_end = tn_end;
-      if (kPrefetch) {
-        lo = lo1;
-        hi = hi1;
-        start = start1;
-#pragma unroll
-        for (uint32_t u = 0; u < kUnroll; ++u) v[u] = v1[u];
-      }
     }
     __syncthreads();
   }

@@ -99,6 +99,22 @@ def test_4bit_lanes_short_queries():
     assert_same(res, oracle.topk(w))
 
 
+# Small vocabularies make counts reach the bound B.  B = 7, 127 (and 256 in
+# 16-bit lanes) leave every lane's top bit free, so the Gate tests whole
+# counter words; B = 8, 15, 128, 255 do not, so it tests each posting's lane.
+@pytest.mark.parametrize("vocab,obj_len,b", [
+    (12, (3, 11), 7), (20, (5, 18), 8), (20, (5, 19), 15),
+    (160, (60, 150), 127), (300, (100, 290), 128), (300, (100, 290), 255),
+    (300, (100, 290), 256)])
+def test_gate_test_on_both_sides_of_lane_headroom(vocab, obj_len, b):
+    w = synth.sets(50_000, obj_len, vocab, 32, (b, b), 10, config=200 + b)
+    res, _, qs = run(w, chunk_shift=12)
+    assert qs.max_bound == b
+    ref = oracle.topk(w)
+    assert ref["counts"][:, 0].max() >= b - 3  # counts near the bound
+    assert_same(res, ref)
+
+
 # ---------------------------------------------------------------------------
 # c-PQ invariants on the device state
 # ---------------------------------------------------------------------------
