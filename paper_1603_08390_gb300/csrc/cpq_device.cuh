@@ -320,6 +320,55 @@ __device__ __noinline__ void publish_seed(uint32_t* hh, uint32_t* seed,
   if (threadIdx.x == 0 && x) atomicMax(seed, x);
 }
 
+// Old counter words of one lane's 4 * U postings in a tile.
+template <int U>
+struct TileWords {
+  uint32_t w[4 * U];
+};
+
+// The exact Gate test of a tile whose word test may have passed, kept out of
+// line so that the scan loop's registers and code stay those of the common
+// case.  Slot i of the lane is posting c_start + (i / 4 * 32 + lane) * 4 +
+// i % 4 of the List Array; it passes when it lies in [c_lo, c_hi) and its own
+// lane of val.w[i], plus one, reaches at_c.  The passing slots run the Gate in
+// ascending slot order (ids reloaded from L1).  All lanes of the warp call it.
+// Returns (Gate passes, hash-table inserts).
+template <int LOG2W, int U>
+__device__ __noinline__ uint2 gate_tile(const GateState g, const uint32_t* __restrict__ post_ids,
+                                        uint32_t c_start, uint32_t c_lo, uint32_t c_hi,
+                                        const TileWords<U> val, uint32_t at_c, uint32_t kq,
+                                        uint32_t B, uint32_t obj_base, uint32_t ht_mask,
+                                        uint32_t ht_bits) {
+  const uint32_t lane = dev::lane_id();
+  const uint32_t d0 = c_start + lane * 4 - c_lo, len = c_hi - c_lo;
+  uint32_t pm = 0;  // this lane's passing slots
+#pragma unroll
+  for (uint32_t u = 0; u < U; ++u) {
+    const uint32_t idx = c_start + (u * 32 + lane) * 4;
+    const uint4 w = idx < c_hi ? __ldg(reinterpret_cast<const uint4*>(post_ids + idx))
+                               : make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (uint32_t e = 0; e < 4; ++e) {
+      const uint32_t i = u * 4 + e;
+      const uint32_t id = e == 0 ? w.x : e == 1 ? w.y : e == 2 ? w.z : w.w;
+      pm |= (uint32_t)(d0 + u * 128 + e < len &&
+                       Lane<LOG2W>::pick(val.w[i], Lane<LOG2W>::sel(id)) + 1 >= at_c)
+            << i;
+    }
+  }
+  uint32_t n_gate = 0, n_ins = 0;
+  for (uint32_t m = pm; m; m &= m - 1) {
+    const uint32_t i = __ffs(m) - 1;
+    uint32_t word = 0;
+#pragma unroll
+    for (uint32_t j = 0; j < 4 * U; ++j) word = j == i ? val.w[j] : word;
+    const uint32_t id = __ldg(post_ids + c_start + ((i >> 2) * 32 + lane) * 4 + (i & 3));
+    gate_pass<LOG2W>(g, id, Lane<LOG2W>::pick(word, Lane<LOG2W>::sel(id)) + 1, kq, B, obj_base,
+                     ht_mask, ht_bits, n_gate, n_ins);
+  }
+  return make_uint2(n_gate, n_ins);
+}
+
 // LOG2W: log2 of the counter width; U: 16-byte loads in flight per lane (a
 // warp tile is 128 * U postings); THREADS: block size.
 // Static shared state of one block.
@@ -534,35 +583,13 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
           hit = (acc & Lane<LOG2W>::kHigh) != 0;
         }
         if (__any_sync(0xFFFFFFFFu, hit)) {
-          // the exact test: each slot's own lane, inside the list
-          const uint32_t d0 = c_start + lane * 4 - c_lo, len = c_hi - c_lo;
-          uint32_t pm = 0;  // this lane's passing slots
+          TileWords<U> tw;
 #pragma unroll
-          for (uint32_t u = 0; u < kUnroll; ++u) {
-            const uint32_t idx = c_start + (u * 32 + lane) * 4;
-            const uint4 w = idx < c_hi ? __ldg(reinterpret_cast<const uint4*>(A.post_ids + idx))
-                                       : make_uint4(0, 0, 0, 0);
-#pragma unroll
-            for (uint32_t e = 0; e < 4; ++e) {
-              const uint32_t i = u * 4 + e;
-              const uint32_t id = e == 0 ? w.x : e == 1 ? w.y : e == 2 ? w.z : w.w;
-              pm |= (uint32_t)(d0 + u * 128 + e < len &&
-                               Lane<LOG2W>::pick(val[i], Lane<LOG2W>::sel(id)) + 1 >= at_c)
-                    << i;
-            }
-          }
-          const uint32_t wm = __reduce_or_sync(0xFFFFFFFFu, pm);
-#pragma unroll
-          for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
-            if ((wm >> i) & 1u) {  // some lane passes at slot i
-              const uint32_t u = i >> 2, e = i & 3;
-              if ((pm >> i) & 1u) {
-                const uint32_t id = __ldg(A.post_ids + c_start + (u * 32 + lane) * 4 + e);
-                gate_pass<LOG2W>(gs, id, Lane<LOG2W>::pick(val[i], Lane<LOG2W>::sel(id)) + 1, kq,
-                                 B, obj_base, ht_mask, ht_bits, n_gate, n_ins);
-              }
-            }
-          }
+          for (uint32_t i = 0; i < 4 * kUnroll; ++i) tw.w[i] = val[i];
+          const uint2 d = gate_tile<LOG2W, U>(gs, A.post_ids, c_start, c_lo, c_hi, tw, at_c, kq, B,
+                                              obj_base, ht_mask, ht_bits);
+          n_gate += d.x;
+          n_ins += d.y;
         }
       }
       if (run_ends) run += nwarps;

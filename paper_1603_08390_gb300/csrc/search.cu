@@ -36,10 +36,11 @@
 //    Bitmap Counter, so the result never depends on the hash table's luck.
 //  * Ties at the k-th count are filled in ascending object id from the
 //    Bitmap Counter (the paper breaks them randomly).
-//  * A warp counts a tile of postings, then tests the tile once (does any
-//    lane's largest new count reach AT?) and runs the Gate only for the
-//    slots that pass, one ZipperArray add per pass; the pass that fills a
-//    level to k advances AT.
+//  * A warp counts a tile of postings, then tests the tile once (can any
+//    posting's new count reach AT?  With headroom in the counter lanes this
+//    is one add per old counter word) and runs the Gate only for the slots
+//    that pass, one ZipperArray add per pass; the pass that fills a level to
+//    k advances AT.
 //  * AT seeds: a range that finishes adds the counts it reports to its
 //    query's histogram and publishes the k-th largest of them, a lower bound
 //    of the query's k-th count; later ranges start their AT there, and ties
