@@ -458,6 +458,9 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   // ---- scan: all postings of the query's keywords inside this id range ---
   const uint32_t qa = A.q_off[q], qb = A.q_off[q + 1];
   const uint32_t stride = A.n_chunks + 1;
+  // a register copy: A may live in shared memory (persistent blocks), which
+  // the counter atomics' memory clobbers would make the loop reload
+  const uint32_t* __restrict__ post_ids = A.post_ids;
   // shared address of the counter word of object id: bc_adj + byte_off(id)
   const uint32_t bc_adj =
       (uint32_t)__cvta_generic_to_shared(bc) - Lane<LOG2W>::byte_off(obj_base);
@@ -504,7 +507,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
 #pragma unroll
       for (uint32_t u = 0; u < kUnroll; ++u) {
         const uint32_t idx = st_ + (u * 32 + lane) * 4;
-        if (idx < hi_) vv[u] = __ldg(reinterpret_cast<const uint4*>(A.post_ids + idx));
+        if (idx < hi_) vv[u] = __ldg(reinterpret_cast<const uint4*>(post_ids + idx));
       }
     };
     // One id buffer: the counter updates of a tile take its ids, then the
@@ -586,7 +589,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
           TileWords<U> tw;
 #pragma unroll
           for (uint32_t i = 0; i < 4 * kUnroll; ++i) tw.w[i] = val[i];
-          const uint2 d = gate_tile<LOG2W, U>(gs, A.post_ids, c_start, c_lo, c_hi, tw, at_c, kq, B,
+          const uint2 d = gate_tile<LOG2W, U>(gs, post_ids, c_start, c_lo, c_hi, tw, at_c, kq, B,
                                               obj_base, ht_mask, ht_bits);
           n_gate += d.x;
           n_ins += d.y;
