@@ -387,7 +387,7 @@ extern "C" genie_status genie_autotune(const genie_index* index, const genie_que
   genie_status st = make_plan(index, &probe, k, nullptr, &base);
   if (st != GENIE_OK) return st;
   std::vector<genie_batch_opts> cands;
-  const uint32_t shapes[][2] = {{768, 2}, {768, 4}, {1024, 2}, {1024, 4}, {512, 4}};
+  const uint32_t shapes[][2] = {{768, 2}, {768, 4}, {1024, 2}, {1024, 4}, {512, 4}, {512, 8}};
   for (uint32_t ds = 0; ds < 2; ++ds) {
     uint32_t bs = base.block_shift - ds;
     if (ds && bs < index->chunk_shift) continue;

@@ -828,6 +828,10 @@ __global__ void check_k_kernel(uint32_t n_queries, uint32_t k, const uint32_t* _
     if (k_arr[q] == 0 || k_arr[q] > k) atomicOr(bad, 1u);
 }
 
+// Mean postings per (keyword, object range) from which a search defaults to
+// 512 threads with eight loads per lane instead of 768 with two.
+constexpr double kLongSublist = 4096.0;
+
 struct Plan {
   uint32_t log2w;
   uint32_t unroll;
@@ -855,10 +859,15 @@ genie_status make_plan(const genie_index* idx, const genie_queries* qs, uint32_t
   if (slots & (slots - 1)) return fail(GENIE_ERR_INVALID_ARG, "genie_search: ht_slots must be a power of two");
   if (slots < 32) return fail(GENIE_ERR_INVALID_ARG, "genie_search: ht_slots must be >= 32");
   p->ht_slots = slots;
-  p->threads = (o && o->threads) ? o->threads : 768u;
+  // Default shape from the mean sublist a block scans per keyword: long
+  // sublists go faster with fewer, wider warps (eight 16-byte loads per lane
+  // in flight, less tile bookkeeping per posting), short ones with more warps
+  // and smaller tiles (less waste at the sublist ends).
+  const double seg = qs->n_keywords ? (double)qs->n_entries / ((double)qs->n_keywords * p->n_groups) : 0.0;
+  p->threads = (o && o->threads) ? o->threads : (seg >= kLongSublist ? 512u : 768u);
   if (p->threads != 512 && p->threads != 768 && p->threads != 1024)
     return fail(GENIE_ERR_INVALID_ARG, "genie_search: threads must be 512, 768 or 1024");
-  p->unroll = (o && o->unroll) ? o->unroll : (p->threads == 512 ? 4u : 2u);
+  p->unroll = (o && o->unroll) ? o->unroll : (p->threads == 512 ? 8u : 2u);
   if (p->threads == 512 ? (p->unroll != 4 && p->unroll != 8) : (p->unroll != 2 && p->unroll != 4))
     return fail(GENIE_ERR_INVALID_ARG, "genie_search: unroll must be 2 or 4 (768 or 1024 threads), 4 or 8 (512)");
   p->za_len = B + 2;

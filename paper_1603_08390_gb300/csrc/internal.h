@@ -27,7 +27,8 @@ genie_status search_raw(const genie_index* idx, const uint32_t* q_off, const uin
                         const uint32_t* bound, uint32_t n, uint32_t max_bound, uint32_t k,
                         const uint32_t* d_k, unsigned long long* cand, size_t cand_bytes,
                         uint32_t* at_hint, uint32_t* hint_hist, size_t hint_hist_words,
-                        uint32_t* ids, uint32_t* counts, uint32_t* n_valid, cudaStream_t s);
+                        uint32_t* ids, uint32_t* counts, uint32_t* n_valid, cudaStream_t s,
+                        uint64_t n_entries = 0, uint64_t n_keywords = 0);
 
 // Largest per-query count histograms (bytes) a search allocates to seed the
 // AuditThreshold of later object ranges; beyond it the seed is the largest

@@ -179,11 +179,14 @@ genie_status search_raw(const genie_index* idx, const uint32_t* q_off, const uin
                         const uint32_t* bound, uint32_t n, uint32_t max_bound, uint32_t k,
                         const uint32_t* d_k, unsigned long long* cand, size_t cand_bytes,
                         uint32_t* at_hint, uint32_t* hint_hist, size_t hint_hist_words,
-                        uint32_t* ids, uint32_t* counts, uint32_t* n_valid, cudaStream_t s) {
+                        uint32_t* ids, uint32_t* counts, uint32_t* n_valid, cudaStream_t s,
+                        uint64_t n_entries, uint64_t n_keywords) {
   genie_queries view;
   view.index = idx;
   view.n_queries = n;
   view.max_bound = max_bound;
+  view.n_entries = n_entries;  // postings and keywords of the batch (0 if unknown): they pick
+  view.n_keywords = n_keywords;  // the default launch shape
   view.q_off = const_cast<uint32_t*>(q_off);
   view.q_kw = const_cast<uint32_t*>(q_kw);
   view.bound = const_cast<uint32_t*>(bound);

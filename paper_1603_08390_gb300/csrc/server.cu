@@ -32,6 +32,7 @@ double now_s() {
 
 struct Request {
   std::vector<uint32_t> kw;
+  uint64_t entries = 0;  // postings its keywords' lists hold
   uint32_t k = 0;
   uint32_t bound = 0;
   uint64_t tag = 0;
@@ -71,6 +72,7 @@ struct genie_server {
   const genie_index* index = nullptr;
   genie_server_opts opts{};
   int device = 0;
+  std::vector<uint64_t> kw_off;  // host copy of the index's list offsets (postings per request)
   std::vector<genie::Slot> slots;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -114,8 +116,10 @@ void free_slot(Slot& s) {
 void launch_slot(genie_server* sv, Slot& s) {
   const uint32_t n = (uint32_t)s.reqs.size(), kmax = sv->opts.k_max;
   uint32_t pos = 0, max_bound = 1;
+  uint64_t entries = 0;
   for (uint32_t i = 0; i < n; ++i) {
     const Request& r = s.reqs[i];
+    entries += r.entries;
     s.h_q_off[i] = pos;
     std::memcpy(s.h_q_kw + pos, r.kw.data(), r.kw.size() * 4);
     pos += (uint32_t)r.kw.size();
@@ -131,7 +135,7 @@ void launch_slot(genie_server* sv, Slot& s) {
   cudaMemcpyAsync(s.karr, s.h_karr, n * 4, cudaMemcpyHostToDevice, st);
   genie_status gs = search_raw(sv->index, s.q_off, s.q_kw, s.bound, n, max_bound, kmax, s.karr,
                                s.cand, s.cand_bytes, s.hint, s.hint_hist, s.hint_hist_words, s.ids,
-                               s.counts, s.n_valid, st);
+                               s.counts, s.n_valid, st, entries, pos);
   if (gs != GENIE_OK) sv->error = gs;
   cudaMemcpyAsync(s.h_ids, s.ids, (size_t)n * kmax * 4, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(s.h_counts, s.counts, (size_t)n * kmax * 4, cudaMemcpyDeviceToHost, st);
@@ -257,6 +261,13 @@ extern "C" genie_status genie_server_create(const genie_index* index, const geni
   const size_t kw_cap = (size_t)o.max_batch * o.max_query_keywords;
   sv->slots.resize(o.streams);
   cudaError_t e = cudaSuccess;
+  try {
+    sv->kw_off.resize((size_t)index->vocab + 1);
+  } catch (...) {
+    delete sv;
+    return fail(GENIE_ERR_OUT_OF_MEMORY, "genie_server_create: host allocation");
+  }
+  e = cudaMemcpy(sv->kw_off.data(), index->kw_off, sv->kw_off.size() * 8, cudaMemcpyDeviceToHost);
   for (Slot& s : sv->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
@@ -315,8 +326,10 @@ extern "C" genie_status genie_server_submit(genie_server* sv, const uint32_t* h_
     return fail(GENIE_ERR_INVALID_ARG, "genie_server_submit: query longer than max_query_keywords");
   Request r;
   r.kw.assign(h_kw, h_kw + n_kw);
-  for (uint32_t v : r.kw)
+  for (uint32_t v : r.kw) {
     if (v >= sv->index->vocab) return fail(GENIE_ERR_INVALID_ARG, "genie_server_submit: keyword >= vocab");
+    r.entries += sv->kw_off[v + 1] - sv->kw_off[v];
+  }
   // count bound as in genie_make_queries
   const uint64_t cap = (uint64_t)sv->index->max_object_len * max_multiplicity(r.kw);
   r.bound = (uint32_t)std::min<uint64_t>(n_kw, cap);
