@@ -92,7 +92,9 @@ typedef struct {
  *              object, any order.
  *   n_objects  1 .. 2^31; vocab 1 .. 2^31.
  *   chunk_shift  log2 of the object-id range of one sublist (the unit a
- *              search block counts on chip): 12..20, or 0 for the default 15.
+ *              search block counts on chip): 12..20, or 0 for the default 16
+ *              (the 64K-object range of a block with 16-bit counters; a
+ *              search's object range is at least one chunk).
  *   out        receives the index handle (library-owned; free it with
  *              genie_index_destroy).  Unchanged on failure.
  *

@@ -199,7 +199,7 @@ extern "C" genie_status genie_build_index(const uint32_t* d_obj_off, const uint3
     return fail(GENIE_ERR_INVALID_ARG, "genie_build_index: n_objects must be in 1..2^31");
   if (vocab == 0 || vocab > (1u << 31))
     return fail(GENIE_ERR_INVALID_ARG, "genie_build_index: vocab must be in 1..2^31");
-  if (chunk_shift == 0) chunk_shift = 15;
+  if (chunk_shift == 0) chunk_shift = 16;  // the object range of a 16-bit-counter block
   if (chunk_shift < 12 || chunk_shift > 20)
     return fail(GENIE_ERR_INVALID_ARG, "genie_build_index: chunk_shift must be 0 or 12..20");
   cudaStream_t s = as_stream(stream);

@@ -36,8 +36,9 @@ def _row(ids, cnt, n):
 def test_each_result_is_the_same_alone_and_in_the_mix(served):
     w, idx = served
     n_obj = w.n_objects
-    # budget for 48 queries of 8-bit counters in flight
-    opts = genie.ServerOpts(bc_budget_bytes=48 * n_obj, bits_per_object=8, max_batch=32,
+    # budget for 8 queries of 8-bit counters in flight: a quarter of one slot's batch, so the
+    # burst below must be held back however fast the device serves it
+    opts = genie.ServerOpts(bc_budget_bytes=8 * n_obj, bits_per_object=8, max_batch=32,
                             k_max=100, streams=3)
     srv = genie.Server(idx, opts)
     q_off = w.q_off.astype(np.int64)
@@ -52,13 +53,12 @@ def test_each_result_is_the_same_alone_and_in_the_mix(served):
         assert info.tag == i and info.k == w.k[i]
         alone[i] = (info.n_valid,) + _row(ids, cnt, info.n_valid)
     # in the mix: Poisson arrivals at 5M requests/s, all within about 50 us, so
-    # every request is queued while earlier batches run and the budget must
-    # hold some back whatever the service rate
+    # requests queue while earlier batches run and the budget holds some back
     rng = np.random.default_rng(6)
     arrival = np.cumsum(rng.exponential(1.0 / 5e6, w.n_queries))
     lat, ids, cnt, nv = srv.replay(w.q_off, w.q_kw, w.k, arrival)
     st = srv.stats()
-    assert st.max_queries_in_flight <= 48
+    assert st.max_queries_in_flight <= 8
     assert st.deferred_admissions > 0       # the budget held requests back
     assert st.launches < 2 * w.n_queries    # requests were batched together
     assert np.all(lat > 0)
