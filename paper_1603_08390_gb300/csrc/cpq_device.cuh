@@ -369,8 +369,6 @@ __device__ __noinline__ uint2 gate_tile(const GateState g, const uint32_t* __res
   return make_uint2(n_gate, n_ins);
 }
 
-// LOG2W: log2 of the counter width; U: 16-byte loads in flight per lane (a
-// warp tile is 128 * U postings); THREADS: block size.
 // Static shared state of one block.
 struct BlockShared {
   uint32_t at;        // AuditThreshold
@@ -687,6 +685,9 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   }
 }
 
+// One block per (query, object range).  LOG2W: log2 of the counter width; U:
+// 16-byte loads in flight per lane (a warp tile is 128 * U postings);
+// THREADS: the block size.
 template <int LOG2W, int U, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1) scan_cpq_kernel(const ScanArgs A) {
   extern __shared__ uint4 smem_raw[];

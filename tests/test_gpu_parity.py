@@ -115,6 +115,21 @@ def test_gate_test_on_both_sides_of_lane_headroom(vocab, obj_len, b):
     assert_same(res, ref)
 
 
+# Every launch shape the library compiles (threads x 16-byte loads per lane),
+# on both sides of the lane-headroom limit, with ragged sublists and per-query k.
+@pytest.mark.parametrize("threads,unroll", [(768, 2), (768, 4), (1024, 2), (1024, 4), (512, 4),
+                                            (512, 8)])
+@pytest.mark.parametrize("b", [127, 200])
+def test_every_launch_shape(threads, unroll, b):
+    w = synth.sets(70_001, (60, 240), 260, 24, (b, b), 10, config=300 + b)
+    rng = np.random.default_rng(b)
+    w.k = np.array([1, 10, 37], dtype=np.uint32)[rng.integers(0, 3, w.n_queries)]
+    res, _, qs = run(w, chunk_shift=13,
+                     opts=genie.make_opts(threads=threads, unroll=unroll, block_shift=15))
+    assert qs.max_bound == b
+    assert_same(res, oracle.topk(w))
+
+
 # ---------------------------------------------------------------------------
 # c-PQ invariants on the device state
 # ---------------------------------------------------------------------------
