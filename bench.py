@@ -335,6 +335,7 @@ def run_genie(args, rank, world, local):
     # c-PQ counters from one more (untimed) pass
     stats = torch.zeros(8, dtype=torch.int64, device="cuda")
     qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
+    kernel = genie.genie_search_shape(idx, qs, K).kernel_name()
     genie.genie_search(idx, qs, K, out.ids, out.counts, out.n_valid,
                        opts=genie.make_opts(d_stats=stats), stream=stream)
     st = stats.cpu().numpy()
@@ -358,7 +359,7 @@ def run_genie(args, rank, world, local):
                        "batch_p99": float(np.percentile(per_step, 99))},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic_from_profile(),
-                     "kernel": "scan_cpq_kernel<4, 2, 768>", "peak_kind": peak_kind + " hbm_gbs",
+                     "kernel": kernel, "peak_kind": peak_kind + " hbm_gbs",
                      "scan_ms": scan_ms, "algorithmic_bytes_per_launch": algo_bytes},
         "smem_atomic_roofline": {
             "bound": "shared-memory atomic adds (one per posting)",

@@ -200,9 +200,10 @@ typedef struct {
    * s = 1 (this synchronises `stream` once to read the rerun count). */
   const uint32_t* d_seed;
   /* Tuning (0 = automatic): log2 of object ids counted by one block, threads
-   * per block (512, 768 or 1024), hash-table slots per block (power of two
-   * >= 32), 16-byte loads in flight per thread (2 or 4 with 768 or 1024
-   * threads, 4 or 8 with 512). */
+   * per block (512, 768, 896 or 1024), hash-table slots per block (power of
+   * two >= 32), 16-byte loads in flight per thread (2 or 4 with 768 or 1024
+   * threads, 2 with 896, 4 or 8 with 512).  genie_search_shape reports what
+   * the automatic choice is. */
   uint32_t block_shift;
   uint32_t threads;
   uint32_t ht_slots;
@@ -260,6 +261,29 @@ typedef struct {
 genie_status genie_search(const genie_index* index, const genie_queries* queries, uint32_t k,
                           const uint32_t* d_k, const genie_search_opts* opts, uint32_t* d_ids,
                           uint32_t* d_counts, uint32_t* d_n_valid, genie_stream stream);
+
+/* The launch shape of the scan kernel genie_search runs for these arguments. */
+typedef struct {
+  uint32_t counter_bits;   /* bits per object counter: 4, 8 or 16 */
+  uint32_t block_shift;    /* log2 of the object ids one block counts */
+  uint32_t n_groups;       /* object ranges (blocks) per query */
+  uint32_t threads;        /* threads per block */
+  uint32_t unroll;         /* 16-byte loads in flight per thread */
+  uint32_t ht_slots;       /* hash-table slots per block */
+  uint64_t smem_bytes;     /* dynamic shared memory per block */
+} genie_search_shape_info;
+
+/*
+ * Fills *out with the shape genie_search(index, queries, k, ..., opts, ...)
+ * would launch (opts may be NULL).  Host only: no device work, no
+ * synchronisation.  Automatic choices: counters wide enough for the largest
+ * count bound; 128 KB of counters per block; 512 threads with eight loads per
+ * lane when a block's mean sublist per keyword holds at least 4096 postings,
+ * else 896 threads with two (768 with 4-bit counters).  Errors: INVALID_ARG
+ * (NULL handles, k, handles from another index, tuning values out of range).
+ */
+genie_status genie_search_shape(const genie_index* index, const genie_queries* queries, uint32_t k,
+                                const genie_search_opts* opts, genie_search_shape_info* out);
 
 /* ------------------------------------------------------------------------ */
 /* Device calibration                                                        */

@@ -120,6 +120,7 @@ cudaError_t batch_width(const BatchDesc* d, uint32_t blocks, size_t smem, uint32
                                          : launch_batch<LOG2W, 4, 512>(d, blocks, smem, s, launch);
   if (threads == 768) return unroll == 4 ? launch_batch<LOG2W, 4, 768>(d, blocks, smem, s, launch)
                                          : launch_batch<LOG2W, 2, 768>(d, blocks, smem, s, launch);
+  if (threads == 896) return launch_batch<LOG2W, 2, 896>(d, blocks, smem, s, launch);
   return unroll == 4 ? launch_batch<LOG2W, 4, 1024>(d, blocks, smem, s, launch)
                      : launch_batch<LOG2W, 2, 1024>(d, blocks, smem, s, launch);
 }
@@ -387,7 +388,8 @@ extern "C" genie_status genie_autotune(const genie_index* index, const genie_que
   genie_status st = make_plan(index, &probe, k, nullptr, &base);
   if (st != GENIE_OK) return st;
   std::vector<genie_batch_opts> cands;
-  const uint32_t shapes[][2] = {{768, 2}, {768, 4}, {1024, 2}, {1024, 4}, {512, 4}, {512, 8}};
+  const uint32_t shapes[][2] = {{768, 2}, {768, 4}, {896, 2}, {1024, 2}, {1024, 4}, {512, 4},
+                                {512, 8}};
   for (uint32_t ds = 0; ds < 2; ++ds) {
     uint32_t bs = base.block_shift - ds;
     if (ds && bs < index->chunk_shift) continue;

@@ -830,7 +830,7 @@ __global__ void check_k_kernel(uint32_t n_queries, uint32_t k, const uint32_t* _
 }
 
 // Mean postings per (keyword, object range) from which a search defaults to
-// 512 threads with eight loads per lane instead of 768 with two.
+// 512 threads with eight loads per lane instead of 896 (or 768) with two.
 constexpr double kLongSublist = 4096.0;
 
 struct Plan {
@@ -863,12 +863,17 @@ genie_status make_plan(const genie_index* idx, const genie_queries* qs, uint32_t
   // Default shape from the mean sublist a block scans per keyword: long
   // sublists go faster with fewer, wider warps (eight 16-byte loads per lane
   // in flight, less tile bookkeeping per posting), short ones with more warps
-  // and smaller tiles (less waste at the sublist ends).
+  // and smaller tiles (less waste at the sublist ends): 896 threads, as many
+  // as fit without spilling registers, except with 4-bit counters, whose lane
+  // arithmetic needs the registers of 768.
   const double seg = qs->n_keywords ? (double)qs->n_entries / ((double)qs->n_keywords * p->n_groups) : 0.0;
-  p->threads = (o && o->threads) ? o->threads : (seg >= kLongSublist ? 512u : 768u);
-  if (p->threads != 512 && p->threads != 768 && p->threads != 1024)
-    return fail(GENIE_ERR_INVALID_ARG, "genie_search: threads must be 512, 768 or 1024");
+  const uint32_t short_threads = p->log2w >= 3 ? 896u : 768u;
+  p->threads = (o && o->threads) ? o->threads : (seg >= kLongSublist ? 512u : short_threads);
+  if (p->threads != 512 && p->threads != 768 && p->threads != 896 && p->threads != 1024)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search: threads must be 512, 768, 896 or 1024");
   p->unroll = (o && o->unroll) ? o->unroll : (p->threads == 512 ? 8u : 2u);
+  if (p->threads == 896 && p->unroll != 2)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search: 896 threads run two loads per lane");
   if (p->threads == 512 ? (p->unroll != 4 && p->unroll != 8) : (p->unroll != 2 && p->unroll != 4))
     return fail(GENIE_ERR_INVALID_ARG, "genie_search: unroll must be 2 or 4 (768 or 1024 threads), 4 or 8 (512)");
   p->za_len = B + 2;

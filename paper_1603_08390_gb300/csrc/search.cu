@@ -90,6 +90,7 @@ cudaError_t dispatch_width(const ScanArgs& a, const Plan& p, cudaStream_t s) {
                                              : launch_scan<LOG2W, 4, 512>(a, p, s);
   if (p.threads == 768) return p.unroll == 4 ? launch_scan<LOG2W, 4, 768>(a, p, s)
                                              : launch_scan<LOG2W, 2, 768>(a, p, s);
+  if (p.threads == 896) return launch_scan<LOG2W, 2, 896>(a, p, s);
   return p.unroll == 4 ? launch_scan<LOG2W, 4, 1024>(a, p, s) : launch_scan<LOG2W, 2, 1024>(a, p, s);
 }
 
@@ -209,6 +210,27 @@ genie_status search_raw(const genie_index* idx, const uint32_t* q_off, const uin
 }  // namespace genie
 
 using namespace genie;
+
+extern "C" genie_status genie_search_shape(const genie_index* index, const genie_queries* queries,
+                                           uint32_t k, const genie_search_opts* opts,
+                                           genie_search_shape_info* out) {
+  if (!index || !queries || !out) return fail(GENIE_ERR_INVALID_ARG, "genie_search_shape: NULL argument");
+  if (queries->index != index)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search_shape: queries were compiled for another index");
+  if (k == 0 || k > GENIE_MAX_K)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search_shape: k must be in 1..GENIE_MAX_K");
+  Plan p;
+  genie_status st = make_plan(index, queries, k, opts, &p);
+  if (st != GENIE_OK) return st;
+  out->counter_bits = 1u << p.log2w;
+  out->block_shift = p.block_shift;
+  out->n_groups = p.n_groups;
+  out->threads = p.threads;
+  out->unroll = p.unroll;
+  out->ht_slots = p.ht_slots;
+  out->smem_bytes = p.smem;
+  return GENIE_OK;
+}
 
 extern "C" genie_status genie_search(const genie_index* index, const genie_queries* queries,
                                      uint32_t k, const uint32_t* d_k, const genie_search_opts* opts,

@@ -32,7 +32,7 @@ EXPORTED = (
     "genie_last_error", "genie_version", "genie_build_index", "genie_index_destroy",
     "genie_index_get_info", "genie_index_export", "genie_make_queries", "genie_compile_ranges",
     "genie_queries_destroy", "genie_queries_get_info", "genie_queries_export", "genie_search",
-    "genie_search_noalloc", "genie_mlp_num_params", "genie_mlp_create", "genie_mlp_destroy",
+    "genie_search_shape", "genie_search_noalloc", "genie_mlp_num_params", "genie_mlp_create", "genie_mlp_destroy",
     "genie_mlp_set_params", "genie_mlp_get_params", "genie_mlp_forward", "genie_mlp_gradients",
     "genie_mlp_adam_step", "genie_mlp_train", "genie_mlp_seeds", "genie_autotune",
     "genie_batch_create", "genie_batch_get_info", "genie_batch_destroy", "genie_batch_run",
@@ -109,6 +109,18 @@ class SearchOpts(ctypes.Structure):
                 ("flags", ctypes.c_uint32)]
 
 
+class SearchShape(ctypes.Structure):
+    _fields_ = [("counter_bits", ctypes.c_uint32), ("block_shift", ctypes.c_uint32),
+                ("n_groups", ctypes.c_uint32), ("threads", ctypes.c_uint32),
+                ("unroll", ctypes.c_uint32), ("ht_slots", ctypes.c_uint32),
+                ("smem_bytes", ctypes.c_uint64)]
+
+    def kernel_name(self) -> str:
+        """Name of the scan kernel this shape launches, as profilers print it."""
+        log2w = {4: 2, 8: 3, 16: 4}[self.counter_bits]
+        return "scan_cpq_kernel<%d, %d, %d>" % (log2w, self.unroll, self.threads)
+
+
 _LIB = None
 _LOCK = threading.Lock()
 
@@ -150,6 +162,9 @@ def load(path: Optional[str] = None):
         lib.genie_search.restype = st
         lib.genie_search_noalloc.argtypes = lib.genie_search.argtypes
         lib.genie_search_noalloc.restype = st
+        lib.genie_search_shape.argtypes = [vp, vp, u32, ctypes.POINTER(SearchOpts),
+                                           ctypes.POINTER(SearchShape)]
+        lib.genie_search_shape.restype = st
         f32 = ctypes.c_float
         lib.genie_mlp_num_params.restype = u32
         lib.genie_mlp_num_params.argtypes = []
@@ -359,6 +374,17 @@ def genie_search(index: Index, queries: Queries, k: int, d_ids, d_counts, d_n_va
     _check(lib.genie_search(index.handle, queries.handle, k, _ptr(d_k),
                             ctypes.byref(opts) if opts is not None else None, _ptr(d_ids),
                             _ptr(d_counts), _ptr(d_n_valid), _stream(stream)), lib)
+
+
+def genie_search_shape(index: Index, queries: Queries, k: int,
+                       opts: Optional[SearchOpts] = None) -> SearchShape:
+    """The scan kernel's launch shape genie_search would use (host only)."""
+    lib = load()
+    out = SearchShape()
+    _check(lib.genie_search_shape(index.handle, queries.handle, k,
+                                  ctypes.byref(opts) if opts is not None else None,
+                                  ctypes.byref(out)), lib)
+    return out
 
 
 def genie_search_noalloc(index: Index, queries: Queries, k: int, d_ids, d_counts, d_n_valid,

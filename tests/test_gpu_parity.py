@@ -117,8 +117,8 @@ def test_gate_test_on_both_sides_of_lane_headroom(vocab, obj_len, b):
 
 # Every launch shape the library compiles (threads x 16-byte loads per lane),
 # on both sides of the lane-headroom limit, with ragged sublists and per-query k.
-@pytest.mark.parametrize("threads,unroll", [(768, 2), (768, 4), (1024, 2), (1024, 4), (512, 4),
-                                            (512, 8)])
+@pytest.mark.parametrize("threads,unroll", [(768, 2), (768, 4), (896, 2), (1024, 2), (1024, 4),
+                                            (512, 4), (512, 8)])
 @pytest.mark.parametrize("b", [127, 200])
 def test_every_launch_shape(threads, unroll, b):
     w = synth.sets(70_001, (60, 240), 260, 24, (b, b), 10, config=300 + b)
@@ -128,6 +128,40 @@ def test_every_launch_shape(threads, unroll, b):
                      opts=genie.make_opts(threads=threads, unroll=unroll, block_shift=15))
     assert qs.max_bound == b
     assert_same(res, oracle.topk(w))
+
+
+def test_search_shape_reports_the_automatic_choice():
+    # short sublists (LSH buckets, one object range): 896 threads, two loads per lane
+    w = synth.lsh(60_000, 8, 10, config=12)
+    idx = runner.build_index(w)
+    qs = runner.compile_queries(idx, w)
+    sh = genie.genie_search_shape(idx, qs, 10)
+    assert (sh.counter_bits, sh.threads, sh.unroll) == (16, 896, 2)
+    assert sh.kernel_name() == "scan_cpq_kernel<4, 2, 896>"
+    blocks = genie.make_opts()
+    runner.search(idx, qs, 10, opts=blocks)
+    torch.cuda.synchronize()
+    assert blocks._blocks.value == sh.n_groups == 1
+    # explicit tuning is taken as given, and checked
+    sh = genie.genie_search_shape(idx, qs, 10, genie.make_opts(threads=1024, unroll=4))
+    assert (sh.threads, sh.unroll) == (1024, 4)
+    with pytest.raises(genie.GenieError) as e:
+        genie.genie_search_shape(idx, qs, 10, genie.make_opts(threads=896, unroll=4))
+    assert e.value.status == genie.GENIE_ERR_INVALID_ARG
+    # long sublists (a small vocabulary): 512 threads, eight loads per lane
+    w = synth.sets(50_000, (100, 290), 300, 8, (128, 128), 10, config=201)
+    idx = runner.build_index(w)
+    qs = runner.compile_queries(idx, w)
+    sh = genie.genie_search_shape(idx, qs, 10)
+    assert (sh.counter_bits, sh.threads, sh.unroll) == (8, 512, 8)
+    # 4-bit counters keep 768 threads for short sublists (3 items of 5 values: B = 15)
+    w = synth.relational(n_objects=70_001, n_queries=8, config=11, items_per_query=3)
+    idx = runner.build_index(w)
+    qs = runner.compile_queries(idx, w)
+    assert qs.max_bound <= 15
+    sh = genie.genie_search_shape(idx, qs, 10)
+    assert (sh.counter_bits, sh.threads, sh.unroll) == (4, 768, 2)
+    assert_same(runner.search(idx, qs, 10).host(), oracle.topk(w))
 
 
 # ---------------------------------------------------------------------------
