@@ -279,7 +279,7 @@ typedef struct {
  * synchronisation.  Automatic choices: counters wide enough for the largest
  * count bound; 128 KB of counters per block; 512 threads with eight loads per
  * lane when a block's mean sublist per keyword holds at least 4096 postings,
- * else 896 threads with two (768 with 4-bit counters).  Errors: INVALID_ARG
+ * else 1024 threads with two (768 with 4-bit counters).  Errors: INVALID_ARG
  * (NULL handles, k, handles from another index, tuning values out of range).
  */
 genie_status genie_search_shape(const genie_index* index, const genie_queries* queries, uint32_t k,
@@ -329,9 +329,10 @@ typedef struct {
 } genie_batch_opts;
 
 /*
- * Autotuner: times genie_search on `sample` (compiled queries representative
- * of the workload) for each candidate shape -- block size x 16-byte loads in
- * flight x object-id range per block -- and writes the fastest to *out.
+ * Autotuner: runs `sample` (compiled queries representative of the workload)
+ * as a persistent batch (genie_batch_create + genie_batch_run) for each
+ * candidate shape -- block size x 16-byte loads in flight x object-id range
+ * per block -- and writes the fastest to *out.
  * cache_path (may be NULL): a text file of "key block_shift threads unroll
  * ht_slots ms" lines; a line whose key (GPU, index sizes, count bound, k and
  * the postings-per-query scale) matches is returned without timing, and a

@@ -415,17 +415,15 @@ extern "C" genie_status genie_autotune(const genie_index* index, const genie_que
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   float best = 1e30f;
   genie_batch_opts best_o = cands.empty() ? genie_batch_opts{} : cands[0];
+  // each candidate runs as the persistent batch it would become (its kernel
+  // differs from the one-block-per-item search in registers and scheduling)
   for (size_t c = 0; c < cands.size() && e == cudaSuccess; ++c) {
-    genie_search_opts so;
-    std::memset(&so, 0, sizeof(so));
-    so.block_shift = cands[c].block_shift;
-    so.threads = cands[c].threads;
-    so.unroll = cands[c].unroll;
-    so.ht_slots = cands[c].ht_slots;
+    genie_batch* cb = nullptr;
+    st = genie_batch_create(index, Q, sample->max_bound, k, &cands[c], &cb);
     float t = 1e30f;
-    for (int rep = 0; rep < 3; ++rep) {  // first run warms up
+    for (int rep = 0; rep < 3 && st == GENIE_OK; ++rep) {  // first run warms up
       cudaEventRecord(e0, s);
-      st = genie_search(index, sample, k, nullptr, &so, ids, cnt, nv, (genie_stream)s);
+      st = genie_batch_run(cb, sample, nullptr, ids, cnt, nv, (genie_stream)s);
       cudaEventRecord(e1, s);
       if (st != GENIE_OK) break;
       e = cudaEventSynchronize(e1);
@@ -433,6 +431,7 @@ extern "C" genie_status genie_autotune(const genie_index* index, const genie_que
       cudaEventElapsedTime(&ms, e0, e1);
       if (rep > 0) t = std::min(t, ms);
     }
+    if (cb) genie_batch_destroy(cb);
     if (st != GENIE_OK) { st = GENIE_OK; continue; }  // a shape this GPU cannot run
     cands[c].tuned_ms = t;
     if (t < best) {

@@ -201,6 +201,19 @@ struct GateState {
   uint32_t* flags;    // [0] an insert found no slot, [1] a count above the bound
 };
 
+// What the Gate of one block needs besides a posting, kept in shared memory so
+// that the scan loop does not hold it in registers.
+struct GateCtx {
+  GateState g;
+  uint32_t kq;        // k of the query
+  uint32_t B;         // count bound of the query
+  uint32_t obj_base;  // first object id of the range
+  uint32_t ht_mask;   // hash-table slots - 1
+  uint32_t ht_bits;   // log2 of the hash-table slots
+  uint32_t n_gate;    // Gate passes of the block (statistics)
+  uint32_t n_ins;     // hash-table inserts of the block (statistics)
+};
+
 // Hash-table insert of a candidate id (once per object while it is flagged
 // present).  A slot is free when empty or when its object's exact count has
 // fallen below AT - 1 (Sec. 3.3.2); the evicted object loses its flag.
@@ -331,14 +344,15 @@ struct TileWords {
 // case.  Slot i of the lane is posting c_start + (i / 4 * 32 + lane) * 4 +
 // i % 4 of the List Array; it passes when it lies in [c_lo, c_hi) and its own
 // lane of val.w[i], plus one, reaches at_c.  The passing slots run the Gate in
-// ascending slot order (ids reloaded from L1).  All lanes of the warp call it.
-// Returns (Gate passes, hash-table inserts).
+// ascending slot order (ids reloaded from L1) and are counted into
+// ctx.n_gate and ctx.n_ins.  All lanes of the warp call it.
 template <int LOG2W, int U>
-__device__ __noinline__ uint2 gate_tile(const GateState g, const uint32_t* __restrict__ post_ids,
+__device__ __noinline__ void gate_tile(GateCtx& ctx, const uint32_t* __restrict__ post_ids,
                                         uint32_t c_start, uint32_t c_lo, uint32_t c_hi,
-                                        const TileWords<U> val, uint32_t at_c, uint32_t kq,
-                                        uint32_t B, uint32_t obj_base, uint32_t ht_mask,
-                                        uint32_t ht_bits) {
+                                        const TileWords<U> val, uint32_t at_c) {
+  const GateState g = ctx.g;
+  const uint32_t kq = ctx.kq, B = ctx.B, obj_base = ctx.obj_base, ht_mask = ctx.ht_mask,
+                 ht_bits = ctx.ht_bits;
   const uint32_t lane = dev::lane_id();
   const uint32_t d0 = c_start + lane * 4 - c_lo, len = c_hi - c_lo;
   uint32_t pm = 0;  // this lane's passing slots
@@ -366,7 +380,8 @@ __device__ __noinline__ uint2 gate_tile(const GateState g, const uint32_t* __res
     gate_pass<LOG2W>(g, id, Lane<LOG2W>::pick(word, Lane<LOG2W>::sel(id)) + 1, kq, B, obj_base,
                      ht_mask, ht_bits, n_gate, n_ins);
   }
-  return make_uint2(n_gate, n_ins);
+  if (n_gate) atomicAdd(&ctx.n_gate, n_gate);
+  if (n_ins) atomicAdd(&ctx.n_ins, n_ins);
 }
 
 // Static shared state of one block.
@@ -379,8 +394,8 @@ struct BlockShared {
   uint32_t at0;       // AuditThreshold the range started with
   uint32_t gateless;  // count only, then select from the Bitmap Counter
   uint32_t tie_floor; // ties below it are left out of the read-out
+  GateCtx gate;       // the Gate's pointers and query constants
   uint32_t scratch[33];
-  unsigned long long scratch64[33];
 };
 
 // One (query, object range) work item: reset the range's c-PQ in shared
@@ -398,7 +413,6 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   uint32_t& s_n = S.n;
   uint32_t* s_flags = S.flags;
   uint32_t* scratch = S.scratch;
-  unsigned long long* scratch64 = S.scratch64;
 
   // shared-memory layout: Bitmap Counter | presence bits | Hash Table | read-out
   // buffer | ZipperArray | staged keyword segments
@@ -416,15 +430,16 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   const uint32_t tid = threadIdx.x, lane = dev::lane_id(), warp = dev::warp_id();
   const uint32_t nwarps = blockDim.x >> 5;
   const uint32_t q = A.q_sel ? A.q_sel[qi] : qi;
-  const uint32_t kq = A.k_arr ? A.k_arr[q] : A.k;
-  const uint32_t B = A.bound[q];
-  const uint32_t obj_base = g << A.block_shift;
-  const uint32_t n_local = min(1u << A.block_shift, A.n_objects - obj_base);
   const uint32_t c0 = g * A.chunks_per_block, c1 = min(c0 + A.chunks_per_block, A.n_chunks);
-  const uint32_t ht_mask = A.ht_slots - 1, ht_bits = 31 - __clz(A.ht_slots);
 
   // ---- reset this block's c-PQ ------------------------------------------
+  // The query's k and bound and the range's first id live in S.gate from
+  // here on (the scan loop keeps none of them in registers).
   {
+    const uint32_t kq = A.k_arr ? A.k_arr[q] : A.k;
+    const uint32_t B = A.bound[q];
+    const uint32_t obj_base = g << A.block_shift;
+    const uint32_t ht_mask = A.ht_slots - 1, ht_bits = 31 - __clz(A.ht_slots);
     uint4* b4 = reinterpret_cast<uint4*>(bc);
     const uint4 z4 = make_uint4(0, 0, 0, 0);
     for (uint32_t i = tid; i < ((nwords + npresent) >> 2); i += blockDim.x) b4[i] = z4;
@@ -442,16 +457,14 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
       S.gateless = A.no_gate || (A.at_hint && s_at == 1);
       s_flags[0] = 0;
       s_flags[1] = 0;
+      S.gate = GateCtx{GateState{za, present, ht, bc, &s_at, s_flags}, kq, B, obj_base, ht_mask,
+                       ht_bits, 0u, 0u};
     }
   }
   __syncthreads();
   const bool gateless = S.gateless;
   // every count of the range stays below the top bit of its lane
-  const bool swar = B < (1u << ((1u << LOG2W) - 1));
-
-  uint32_t n_gate = 0, n_ins = 0;
-
-  const GateState gs{za, present, ht, bc, &s_at, s_flags};
+  const bool swar = S.gate.B < (1u << ((1u << LOG2W) - 1));
 
   // ---- scan: all postings of the query's keywords inside this id range ---
   const uint32_t qa = A.q_off[q], qb = A.q_off[q + 1];
@@ -461,7 +474,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   const uint32_t* __restrict__ post_ids = A.post_ids;
   // shared address of the counter word of object id: bc_adj + byte_off(id)
   const uint32_t bc_adj =
-      (uint32_t)__cvta_generic_to_shared(bc) - Lane<LOG2W>::byte_off(obj_base);
+      (uint32_t)__cvta_generic_to_shared(bc) - Lane<LOG2W>::byte_off(S.gate.obj_base);
   for (uint32_t kb = qa; kb < qb; kb += kKwBatch) {
     const uint32_t nk = min(kKwBatch, qb - kb);
     uint32_t ntiles = 0;
@@ -587,10 +600,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
           TileWords<U> tw;
 #pragma unroll
           for (uint32_t i = 0; i < 4 * kUnroll; ++i) tw.w[i] = val[i];
-          const uint2 d = gate_tile<LOG2W, U>(gs, post_ids, c_start, c_lo, c_hi, tw, at_c, kq, B,
-                                              obj_base, ht_mask, ht_bits);
-          n_gate += d.x;
-          n_ins += d.y;
+          gate_tile<LOG2W, U>(S.gate, post_ids, c_start, c_lo, c_hi, tw, at_c);
         }
       }
       if (run_ends) run += nwarps;
@@ -601,6 +611,8 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   }
 
   // ---- finalise AT (Lemma 3.1) and read out this range's top-k ----------
+  const uint32_t kq = S.gate.kq, B = S.gate.B, obj_base = S.gate.obj_base;
+  const uint32_t n_local = min(1u << A.block_shift, A.n_objects - obj_base);
   const uint32_t nwords_local = (n_local + PER - 1) / PER;
   if (gateless) {
     // the k-th count of the range: largest x with #{count >= x} >= k
@@ -671,17 +683,13 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   } else if (A.at_hint && tid == 0 && at_f >= 2) {
     atomicMax(&A.at_hint[qi], at_f - 1);
   }
-  if (A.stats) {
-    unsigned long long gsum = dev::block_sum((unsigned long long)n_gate, scratch64);
-    unsigned long long isum = dev::block_sum((unsigned long long)n_ins, scratch64);
-    if (tid == 0) {
-      atomicAdd(&A.stats[0], gsum);
-      atomicAdd(&A.stats[1], isum);
-      if (!certified && !gateless) atomicAdd(&A.stats[2], 1ull);
-      if (gateless) atomicAdd(&A.stats[6], 1ull);
-      atomicAdd(&A.stats[4], 1ull);
-      if (s_flags[1]) atomicAdd(&A.stats[5], 1ull);
-    }
+  if (A.stats && tid == 0) {
+    atomicAdd(&A.stats[0], (unsigned long long)S.gate.n_gate);
+    atomicAdd(&A.stats[1], (unsigned long long)S.gate.n_ins);
+    if (!certified && !gateless) atomicAdd(&A.stats[2], 1ull);
+    if (gateless) atomicAdd(&A.stats[6], 1ull);
+    atomicAdd(&A.stats[4], 1ull);
+    if (s_flags[1]) atomicAdd(&A.stats[5], 1ull);
   }
 }
 
@@ -830,7 +838,7 @@ __global__ void check_k_kernel(uint32_t n_queries, uint32_t k, const uint32_t* _
 }
 
 // Mean postings per (keyword, object range) from which a search defaults to
-// 512 threads with eight loads per lane instead of 896 (or 768) with two.
+// 512 threads with eight loads per lane instead of 1024 (or 768) with two.
 constexpr double kLongSublist = 4096.0;
 
 struct Plan {
@@ -863,11 +871,11 @@ genie_status make_plan(const genie_index* idx, const genie_queries* qs, uint32_t
   // Default shape from the mean sublist a block scans per keyword: long
   // sublists go faster with fewer, wider warps (eight 16-byte loads per lane
   // in flight, less tile bookkeeping per posting), short ones with more warps
-  // and smaller tiles (less waste at the sublist ends): 896 threads, as many
-  // as fit without spilling registers, except with 4-bit counters, whose lane
+  // and smaller tiles (less waste at the sublist ends): 1024 threads, whose
+  // 64 registers the loop fits, except with 4-bit counters, whose lane
   // arithmetic needs the registers of 768.
   const double seg = qs->n_keywords ? (double)qs->n_entries / ((double)qs->n_keywords * p->n_groups) : 0.0;
-  const uint32_t short_threads = p->log2w >= 3 ? 896u : 768u;
+  const uint32_t short_threads = p->log2w >= 3 ? 1024u : 768u;
   p->threads = (o && o->threads) ? o->threads : (seg >= kLongSublist ? 512u : short_threads);
   if (p->threads != 512 && p->threads != 768 && p->threads != 896 && p->threads != 1024)
     return fail(GENIE_ERR_INVALID_ARG, "genie_search: threads must be 512, 768, 896 or 1024");

@@ -131,13 +131,13 @@ def test_every_launch_shape(threads, unroll, b):
 
 
 def test_search_shape_reports_the_automatic_choice():
-    # short sublists (LSH buckets, one object range): 896 threads, two loads per lane
+    # short sublists (LSH buckets, one object range): 1024 threads, two loads per lane
     w = synth.lsh(60_000, 8, 10, config=12)
     idx = runner.build_index(w)
     qs = runner.compile_queries(idx, w)
     sh = genie.genie_search_shape(idx, qs, 10)
-    assert (sh.counter_bits, sh.threads, sh.unroll) == (16, 896, 2)
-    assert sh.kernel_name() == "scan_cpq_kernel<4, 2, 896>"
+    assert (sh.counter_bits, sh.threads, sh.unroll) == (16, 1024, 2)
+    assert sh.kernel_name() == "scan_cpq_kernel<4, 2, 1024>"
     blocks = genie.make_opts()
     runner.search(idx, qs, 10, opts=blocks)
     torch.cuda.synchronize()
