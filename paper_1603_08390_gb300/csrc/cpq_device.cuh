@@ -58,7 +58,7 @@ struct ScanArgs {
 constexpr uint32_t kMaxProbe = 32;   // hash-table probes before an insert gives up
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kTilePrePad = 36;  // tile prefix sums: sentinels read by a warp-wide step
-constexpr uint32_t kRun = 4;         // consecutive tiles a warp takes as one run
+constexpr uint32_t kRun = 4;         // consecutive tiles a warp claims as one run
 
 size_t scan_smem_bytes(uint32_t log2w, uint32_t block_shift, uint32_t ht_slots, uint32_t za_len,
                        uint32_t k) {
@@ -394,6 +394,7 @@ struct BlockShared {
   uint32_t at0;       // AuditThreshold the range started with
   uint32_t gateless;  // count only, then select from the Bitmap Counter
   uint32_t tie_floor; // ties below it are left out of the read-out
+  uint32_t next_run;  // next run of tiles to be claimed
   GateCtx gate;       // the Gate's pointers and query constants
   uint32_t scratch[33];
 };
@@ -491,13 +492,15 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     if (tid < nk) tile_pre[tid] = pre;
     // after the last keyword: the tile count, then entries no tile reaches
     if (tid <= 32) tile_pre[nk + tid] = tid == 0 ? total_tiles : 0xFFFFFFFFu;
+    if (tid == 0) S.next_run = nwarps;
     __syncthreads();
 
-    // Warp w takes the runs of kRun consecutive tiles w, w + nwarps, ...
-    // (interleaved, so long lists spread over all warps); its tile numbers
+    // Warp w starts with run w of kRun consecutive tiles, then claims the
+    // next unclaimed run from a shared counter (one atomic per run), so warps
+    // that meet Gate passes hold the block back less.  A warp's tile numbers
     // only grow, so its segment cursor j only moves forward: by one test
-    // inside a run, by 32 segments per warp-wide step when it jumps to the
-    // warp's next run.
+    // inside a run, by 32 segments per warp-wide step when it jumps to its
+    // next run.
     uint32_t j = 0;
     auto locate = [&](uint32_t tt, uint32_t& lo_, uint32_t& hi_) -> uint32_t {
       if (tile_pre[j + 1] <= tt) {
@@ -537,7 +540,12 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     while (t < total_tiles) {
       // the tile after t: the next of this run, else the first of the warp's next run
       const bool run_ends = t + 1 >= t_end;
-      const uint32_t tn = run_ends ? (run + nwarps) * kRun : t + 1;
+      if (run_ends) {
+        uint32_t r = 0;
+        if (lane == 0) r = atomicAdd(&S.next_run, 1u);
+        run = __shfl_sync(0xFFFFFFFFu, r, 0);
+      }
+      const uint32_t tn = run_ends ? run * kRun : t + 1;
       const uint32_t tn_end = run_ends ? min(tn + kRun, total_tiles) : t_end;
       // Bitmap Counter: one sub-word atomic add per posting (Algorithm 1,
       // lines 1-2); val = the counter word before the add (0 for slots
@@ -603,7 +611,6 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
           gate_tile<LOG2W, U>(S.gate, post_ids, c_start, c_lo, c_hi, tw, at_c);
         }
       }
-      if (run_ends) run += nwarps;
       t = tn;
       t_end = tn_end;
     }
