@@ -58,7 +58,7 @@ struct ScanArgs {
 constexpr uint32_t kMaxProbe = 32;   // hash-table probes before an insert gives up
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kTilePrePad = 36;  // tile prefix sums: sentinels read by a warp-wide step
-constexpr uint32_t kRun = 4;         // consecutive tiles a warp claims as one run
+constexpr uint32_t kRun = 8;         // consecutive tiles a warp claims as one run
 
 size_t scan_smem_bytes(uint32_t log2w, uint32_t block_shift, uint32_t ht_slots, uint32_t za_len,
                        uint32_t k) {
