@@ -72,7 +72,7 @@ struct genie_server {
   const genie_index* index = nullptr;
   genie_server_opts opts{};
   int device = 0;
-  std::vector<uint64_t> kw_off;  // host copy of the index's list offsets (postings per request)
+  std::vector<uint64_t> kw_off;  // host copy of the list offsets (postings per request), or empty
   std::vector<genie::Slot> slots;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -261,13 +261,15 @@ extern "C" genie_status genie_server_create(const genie_index* index, const geni
   const size_t kw_cap = (size_t)o.max_batch * o.max_query_keywords;
   sv->slots.resize(o.streams);
   cudaError_t e = cudaSuccess;
+  // The host copy of the list offsets only steers the launch shape (postings
+  // per request); without the host memory for it the server runs the default.
   try {
     sv->kw_off.resize((size_t)index->vocab + 1);
   } catch (...) {
-    delete sv;
-    return fail(GENIE_ERR_OUT_OF_MEMORY, "genie_server_create: host allocation");
+    std::vector<uint64_t>().swap(sv->kw_off);
   }
-  e = cudaMemcpy(sv->kw_off.data(), index->kw_off, sv->kw_off.size() * 8, cudaMemcpyDeviceToHost);
+  if (!sv->kw_off.empty())
+    e = cudaMemcpy(sv->kw_off.data(), index->kw_off, sv->kw_off.size() * 8, cudaMemcpyDeviceToHost);
   for (Slot& s : sv->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
@@ -328,7 +330,7 @@ extern "C" genie_status genie_server_submit(genie_server* sv, const uint32_t* h_
   r.kw.assign(h_kw, h_kw + n_kw);
   for (uint32_t v : r.kw) {
     if (v >= sv->index->vocab) return fail(GENIE_ERR_INVALID_ARG, "genie_server_submit: keyword >= vocab");
-    r.entries += sv->kw_off[v + 1] - sv->kw_off[v];
+    if (!sv->kw_off.empty()) r.entries += sv->kw_off[v + 1] - sv->kw_off[v];
   }
   // count bound as in genie_make_queries
   const uint64_t cap = (uint64_t)sv->index->max_object_len * max_multiplicity(r.kw);
