@@ -109,51 +109,82 @@ def workload(rank: int, world: int, n_queries: int = N_QUERIES):
 
 
 class Clocks:
-    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    """nvidia-smi samples of SM clock and throttle reasons, each stamped with
+    the host clock when it arrives; the summary keeps the samples taken inside
+    the timed region (between mark_begin() and mark_end())."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 20
 
     def __init__(self, gpu: int):
         self.gpu = gpu
         self.proc = None
-        self.path = None
+        self.thread = None
+        self.lines = []
+        self.t_begin = self.t_end = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.monotonic(), line))
 
     def start(self):
-        fd, self.path = tempfile.mkstemp(suffix=".csv")
-        os.close(fd)
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
-                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        deadline = time.monotonic() + 5.0  # let the sampler run before the timed region
+        while not self.lines and time.monotonic() < deadline and self.proc.poll() is None:
+            time.sleep(0.01)
+
+    def mark_begin(self):
+        self.t_begin = time.monotonic()
+
+    def mark_end(self):
+        self.t_end = time.monotonic()
 
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(2 * self.INTERVAL_MS / 1e3)  # the sample that covers the region's end
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = []
-        with open(self.path) as f:
-            for line in f:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
-                    rows.append(parts)
-        os.unlink(self.path)
+        self.thread.join(timeout=5)
+        stamped = []
+        for t, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                stamped.append((t, parts))
+        window = "timed region"
+        if self.t_begin is not None and self.t_end is not None:
+            slack = self.INTERVAL_MS / 1e3
+            inside = [p for t, p in stamped if self.t_begin <= t <= self.t_end + slack]
+        else:
+            inside = []
+        if not inside:  # a region shorter than the sampling interval: the samples around it
+            inside = [p for _, p in stamped]
+            window = "whole run (no sample fell inside the timed region)"
+        rows = inside
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
         sm = [float(r[1]) for r in rows]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
-                "reasons": reasons, "samples": len(rows),
-                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+                "reasons": reasons, "samples": len(rows), "window": window,
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()),
+                                   default=None)}
 
 
 KERNEL_SOURCES = ("cpq_device.cuh", "device_util.cuh", "search.cu")
@@ -272,11 +303,13 @@ def run_genie(args, rank, world, local):
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
+    clocks.mark_begin()
     step_ev[0].record(stream)
     for i in range(args.steps):
         step(scan_ev[i])
         step_ev[i + 1].record(stream)
     torch.cuda.synchronize()
+    clocks.mark_end()
     barrier(world)
     clk = clocks.stop()
     total_ms = step_ev[0].elapsed_time(step_ev[-1])
@@ -429,8 +462,10 @@ def run_learned(args, rank, world, local):
         seeded()
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
+    clocks.mark_begin()
     p_ms, _ = timed_steps(plain, args.steps, stream)
     l_ms, per = timed_steps(seeded, args.steps, stream)
+    clocks.mark_end()
     clk = clocks.stop()
     st_p = torch.zeros(8, dtype=torch.int64, device="cuda")
     st_l = torch.zeros(8, dtype=torch.int64, device="cuda")
@@ -502,8 +537,10 @@ def run_parts(args, rank, world, local):
     torch.cuda.synchronize()
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
+    clocks.mark_begin()
     p_ms, per = timed_steps(step_parts, args.steps, stream)
     d_ms, _ = timed_steps(step_device, args.steps, stream)
+    clocks.mark_end()
     clk = clocks.stop()
     a, b = out_p.host(), out_d.host()
     identical = all(np.array_equal(a[key], b[key]) for key in a)
@@ -558,7 +595,9 @@ def run_seq(args, rank, world, local):
     torch.cuda.synchronize()
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
+    clocks.mark_begin()
     ms, per = timed_steps(step, args.steps, stream)
+    clocks.mark_end()
     clk = clocks.stop()
     res = out.host()
     line = {
@@ -642,9 +681,11 @@ def run_batched(args, rank, world, local):
         batched()
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
+    clocks.mark_begin()
     p_ms, _ = timed_steps(plain, args.steps, stream)
     pt_ms, _ = timed_steps(plain_tuned, args.steps, stream)
     b_ms, per = timed_steps(batched, args.steps, stream)
+    clocks.mark_end()
     clk = clocks.stop()
     a, b = out_p.host(), out_b.host()
     identical = all(np.array_equal(a[key], b[key]) for key in a)
@@ -710,6 +751,7 @@ def run_serving(args, rank, world, local):
     sat_qps = n_req / sat_s
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
+    clocks.mark_begin()
     sweep = []
     rng = np.random.default_rng(123)
     for frac in (0.25, 0.5, 0.75, 0.9):
@@ -724,6 +766,7 @@ def run_serving(args, rank, world, local):
                       "p50_ms": float(np.percentile(lat, 50) * 1e3),
                       "p99_ms": float(np.percentile(lat, 99) * 1e3),
                       "mean_ms": float(lat.mean() * 1e3), "results_same_as_saturation": same})
+    clocks.mark_end()
     clk = clocks.stop()
     st = srv.stats()
     qsz = np.diff(q_off.astype(np.int64))
