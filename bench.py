@@ -38,7 +38,7 @@ N_OBJECTS, N_QUERIES, K = 1_000_000, 1024, 100
 WORKLOAD = ("lsh-1m: 1,000,000 objects x 256 p-stable LSH keywords (bucket width 4, "
             "bucket mod 8192), 1024 queries from the same 1000-component mixture, k=100")
 REF_SAMPLE = 32      # oracle queries per reference step
-BASELINE_SAMPLE = 64  # oracle queries for the cpu_baseline object
+CPU_SAMPLE = 64  # oracle queries for the cpu_baseline object
 
 
 def parse():
@@ -408,7 +408,7 @@ def run_genie(args, rank, world, local):
         "cpq": cpq,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, BASELINE_SAMPLE)
+        line["cpu_baseline"] = cpu_baseline(w, CPU_SAMPLE)
     print(json.dumps(line), flush=True)
 
 
