@@ -3,19 +3,31 @@
 
 One step = one batch through the whole path: query compile (keyword look-up,
 count bounds), the fused postings scan + c-PQ kernel and the per-query
-top-k merge, for 1024 LSH queries against 1,000,000 objects x 256 keywords
-(k = 100).  ``value`` is queries/s with the inputs already in HBM; ``e2e``
-is the same through the C ABI from pinned host buffers with the copies
-inside the timed region.  ``--impl reference`` times the CPU oracle on a
-bounded sample of the same workload instead.
+top-k merge.  The headline batch is the largest single-GPU workload of the
+suite: 4096 LSH queries against 4,000,000 objects x 256 keywords (k = 100).
+``value`` is queries/s with the inputs already in HBM; ``e2e`` is the same
+through the C ABI from pinned host buffers (``genie_search_host``: copy in,
+compile, search, copy back, synchronise; one call per batch).
+
+After the headline the default run measures every other workload once, each
+as a sub-object of the same JSON line with its own timing, roofline and an
+oracle check of sampled queries: the 1M-object LSH batch, the batched Zipf
+sets (plain launch vs the persistent graph-captured batch), the learned
+threshold (plain vs seeded on the headline batch), the serving loop
+(saturation and p50/p99 under Poisson arrivals), multiple loadings, the tiny
+relational batch and sequence search.  ``--workload NAME`` runs one of them
+alone; ``--impl reference`` times the CPU oracle on a bounded sample of the
+headline batch instead.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl genie|reference]
 Under torchrun (N > 1) every rank holds an index replica and runs its own
-1024 queries (weak scaling); only the timing uses a (gloo) collective.
+4096 queries (weak scaling); only the timing uses a (gloo) collective, and
+only the headline runs.
 """
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -34,35 +46,29 @@ if ROOT not in sys.path:
 
 METRIC = "match-count top-k queries/s and posting entries/s (% HBM peak); p99 latency"
 UNIT = "queries/s"
-N_OBJECTS, N_QUERIES, K = 1_000_000, 1024, 100
-WORKLOAD = ("lsh-1m: 1,000,000 objects x 256 p-stable LSH keywords (bucket width 4, "
-            "bucket mod 8192), 1024 queries from the same 1000-component mixture, k=100")
-REF_SAMPLE = 32      # oracle queries per reference step
-CPU_SAMPLE = 64  # oracle queries for the cpu_baseline object
+N_OBJECTS, N_QUERIES, K = 4_000_000, 4096, 100
+WORKLOAD = ("lsh-4m: 4,000,000 objects x 256 p-stable LSH keywords (bucket width 4, "
+            "bucket mod 8192), 4096 queries from the same 1000-component mixture, k=100")
+REF_SAMPLE = 16   # oracle queries per reference step
+CPU_SAMPLE = 96   # oracle queries for the cpu_baseline object
+LEGS = ("lsh1m", "sets4m-batched", "lsh4m-learned", "serving", "lsh4m-parts", "relational",
+        "seq1m")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["genie", "reference"], default="genie")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["lsh1m", "lsh4m-learned", "lsh4m-parts",
-                                           "sets4m-batched", "serving", "seq1m"],
-                    default="lsh1m",
-                    help="lsh1m: the headline batch; lsh4m-learned: plain vs learned-seed "
-                         "search on 4M objects / 4096 queries (k=100); lsh4m-parts: the 4M "
-                         "objects as 4 host-resident index parts, 1024 queries, against one "
-                         "device-resident index; seq1m: sequence search by ordered 3-grams "
-                         "with edit-distance verification on 1M sequences; sets4m-batched: plain "
-                         "launch vs the persistent graph-captured batch on 4M Zipf sets / 8192 "
-                         "queries (k=10); serving: continuous-batching server on 8M x 64 Zipf "
-                         "sets, Poisson arrivals at a swept rate, k in {1, 10, 100}")
-    ap.add_argument("--queries", type=int, default=N_QUERIES,
-                    help="queries per batch (the workload is defined at 1024; smaller "
-                         "values are for profiling captures)")
-    return ap.parse_args()
+    ap.add_argument("--workload", choices=("all", "lsh4m") + LEGS, default="all",
+                    help="all: the lsh-4m headline plus every other workload as a sub-object; "
+                         "lsh4m: the headline alone; any other name: that workload alone")
+    ap.add_argument("--queries", type=int, default=0,
+                    help="queries per headline batch (0: the workload's 4096; smaller values "
+                         "are for profiling captures)")
+    return ap.parse_args(argv)
 
 
 def dist_setup():
@@ -100,12 +106,28 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def workload(rank: int, world: int, n_queries: int = N_QUERIES):
+def headline_workload(rank: int, world: int, n_queries: int = N_QUERIES):
+    """The lsh-4m objects and this rank's n_queries queries."""
     import synth
-    w = synth.lsh(N_OBJECTS, n_queries * world, K, config=2)
+    w = synth.lsh(N_OBJECTS, n_queries * world, K, config=4)
     if world > 1:
         w = w.subset(np.arange(rank * n_queries, (rank + 1) * n_queries))
     return w
+
+
+def postings_per_batch(w) -> int:
+    """Postings a batch scans: the sum over query keywords of the keyword's
+    list length (host numpy; the library reports the same from the device)."""
+    df = np.bincount(w.obj_kw, minlength=w.vocab).astype(np.int64)
+    return int(df[w.q_kw].sum())
+
+
+def config_dict(w, world, workload=WORKLOAD, k=K):
+    return {"workload": workload, "n_objects": int(w.n_objects), "n_queries": int(w.n_queries),
+            "k": k, "postings": int(w.nnz),
+            "l2": "inputs larger than L2 (List Array %.2f GB vs 126 MB L2), not flushed" % (
+                w.nnz * 4 / 1e9),
+            "parallelism": "replicas x%d (query batches, no data-path collective)" % world}
 
 
 class Clocks:
@@ -204,10 +226,10 @@ def kernel_source_sha() -> str:
     return h.hexdigest()
 
 
-def traffic_from_profile():
-    """Per-launch DRAM bytes of the scan kernel from the committed ncu summary,
+def traffic_from_profile(name: str = "scan_cpq_lsh4m_ncu.md"):
+    """Per-launch DRAM bytes of the scan kernel from a committed ncu summary,
     valid only while the kernel sources are unchanged since the capture."""
-    p = os.path.join(ROOT, "profiles", "scan_cpq_lsh1m_ncu.md")
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -219,73 +241,108 @@ def traffic_from_profile():
     return float(m_b.group(1)) if kernel_source_sha() == m_sha.group(1) else None
 
 
-def cpu_baseline(w, n_sample: int) -> dict:
-    import oracle
-    sub = w.subset(np.arange(n_sample))
-    oracle.topk(sub.subset(np.arange(2)))  # load and warm
-    t0 = time.perf_counter()
-    oracle.topk(sub)
-    dt = time.perf_counter() - t0
-    return {"value": n_sample / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": "first %d of the %d queries, brute force over all %d objects "
-                      "(%.1f s wall)" % (n_sample, w.n_queries, w.n_objects, dt)}
-
-
-def config_dict(w, world, entries):
-    return {"workload": WORKLOAD, "n_objects": w.n_objects, "n_queries": w.n_queries, "k": K,
-            "postings": int(w.nnz), "entries_per_step": int(entries),
-            "l2": "inputs larger than L2 (index %.2f GB vs 126 MB L2), not flushed" % (
-                (w.nnz * 4 + (w.vocab + 1) * 8 + w.vocab * 33 * 4) / 1e9),
-            "parallelism": "replicas x%d (query batches, no data-path collective)" % world}
-
-
-def run_reference(args, rank, world):
-    if rank != 0:
-        return
-    import oracle
-    w = workload(0, 1)
-    sub = w.subset(np.arange(REF_SAMPLE))
-    oracle.topk(sub.subset(np.arange(2)))
-    times = []
-    for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        oracle.topk(sub)
-        if i >= args.warmup:
-            times.append(time.perf_counter() - t0)
-    step_s = sum(times) / len(times)
-    value = REF_SAMPLE / step_s
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "impl": "reference",
-            "config": config_dict(w, 1, 0),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(),
-                             "kind": "oracle",
-                             "sample": "%d queries per step (first %d of %d), brute force over "
-                                       "%d objects" % (REF_SAMPLE, REF_SAMPLE, w.n_queries,
-                                                       w.n_objects)},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
-def run_genie(args, rank, world, local):
+def timed_steps(step, steps, stream):
+    """CUDA-event time of `steps` calls of step(); returns (total ms, per-step ms)."""
     import torch
-    from paper_1603_08390_gb300 import _build, genie, runner
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for i in range(steps):
+        step()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    return ev[0].elapsed_time(ev[-1]), per
 
-    _build.build()
-    torch.cuda.set_device(local)
-    w = workload(rank, world, args.queries)
+
+def sampled_rows(n_queries: int, n: int = 8):
+    return np.unique(np.linspace(0, n_queries - 1, n).astype(np.int64))
+
+
+def parity_sampled(w, res: dict, rows) -> bool:
+    """Result rows `rows` of `res` (host arrays ids/counts/n_valid, one row per
+    query of w) against the oracle's brute force of the same queries: n_valid
+    equal, and the ranked ids and counts equal up to it."""
+    import oracle
+    ref = oracle.topk(w.subset(rows))
+    for j, q in enumerate(rows):
+        n = int(ref["n_valid"][j])
+        if int(res["n_valid"][q]) != n:
+            return False
+        if not (np.array_equal(res["ids"][q, :n], ref["ids"][j, :n]) and
+                np.array_equal(res["counts"][q, :n], ref["counts"][j, :n])):
+            return False
+    return True
+
+
+def scan_roofline(entries: int, scan_ms: float, kernel: str, traffic=None) -> dict:
+    """The scan kernel against the measured copy peak, in the metric's
+    algorithmic bytes (4 B per posting); DRAM traffic beside it when an ncu
+    capture of the same kernel code gives it."""
+    peak, peak_kind = measured_peaks()
+    algo = 4.0 * entries
+    achieved = algo / (scan_ms / 1e3) / 1e9
+    r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+         "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
+         "peak_kind": peak_kind + " hbm_gbs", "scan_ms": scan_ms,
+         "algorithmic_bytes_per_launch": algo,
+         "bytes": "logical: 4 B per posting scanned; range-major block order serves most of "
+                  "them from L2, so DRAM moves far less (dram_gbs); the binding resource is "
+                  "the shared-memory atomic pipe (smem_atomic_roofline)"}
+    if traffic:
+        r["dram_gbs"] = traffic / (scan_ms / 1e3) / 1e9
+        r["dram_frac"] = r["dram_gbs"] / peak
+    return r
+
+
+def atomic_roofline(entries: int, scan_ms: float, cal) -> dict:
+    rate = entries / (scan_ms / 1e3)
+    return {"bound": "shared-memory atomic adds (one per posting)", "achieved": rate,
+            "peak": cal.smem_atomics_per_s, "unit": "updates/s",
+            "frac": rate / cal.smem_atomics_per_s,
+            "peak_kind": "measured by genie_calibrate on this GPU (atom with return)",
+            "peak_red_no_return": cal.smem_red_per_s}
+
+
+def search_step(genie, idx, d_q_off, d_q_kw, Q, k, out, stream, opts=None, d_k=None):
+    qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
+    genie.genie_search(idx, qs, k, out.ids, out.counts, out.n_valid, d_k=d_k, opts=opts,
+                       stream=stream)
+    return qs
+
+
+def cpq_stats(genie, idx, d_q_off, d_q_kw, Q, k, out, stream, entries, opts_kw=None):
+    """c-PQ counters of one more (untimed) pass."""
+    import torch
+    stats = torch.zeros(8, dtype=torch.int64, device="cuda")
+    search_step(genie, idx, d_q_off, d_q_kw, Q, k, out, stream,
+                opts=genie.make_opts(d_stats=stats, **(opts_kw or {})))
+    st = stats.cpu().numpy()
+    return {"gate_passes_per_posting": float(st[0]) / max(1, entries), "gate_passes": int(st[0]),
+            "ht_inserts": int(st[1]), "blocks": int(st[4]), "blocks_bitmap_fallback": int(st[2]),
+            "blocks_gateless_unseeded": int(st[6]), "reruns": int(st[3]), "bad_ids": int(st[5])}
+
+
+def run_headline(args, rank, world, local, keep=None):
+    """lsh-4m, 4096 queries, k = 100: the headline line.  keep: a dict that
+    receives the workload, index and device queries for the legs that reuse
+    them (learned threshold, multiple loadings)."""
+    import torch
+    from paper_1603_08390_gb300 import genie, runner
+
+    w = headline_workload(rank, world, args.queries or N_QUERIES)
+    t0 = time.perf_counter()
     idx = runner.build_index(w)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
     Q = w.n_queries
     d_q_off, d_q_kw = runner.to_dev(w.q_off), runner.to_dev(w.q_kw)
     out = runner.Outputs(Q, K)
     stream = torch.cuda.current_stream()
 
     def step(events=None):
-        qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
         opts = genie.make_opts(scan_events=events) if events is not None else None
-        genie.genie_search(idx, qs, K, out.ids, out.counts, out.n_valid, opts=opts, stream=stream)
-        return qs
+        return search_step(genie, idx, d_q_off, d_q_kw, Q, K, out, stream, opts=opts)
 
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
@@ -293,6 +350,7 @@ def run_genie(args, rank, world, local):
         qs = step()
     torch.cuda.synchronize()
     entries = qs.n_entries
+    kernel = genie.genie_search_shape(idx, qs, K).kernel_name()
     del qs
     scan_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
@@ -312,144 +370,209 @@ def run_genie(args, rank, world, local):
     clocks.mark_end()
     barrier(world)
     clk = clocks.stop()
+    res = out.host()
     total_ms = step_ev[0].elapsed_time(step_ev[-1])
     per_step = [step_ev[i].elapsed_time(step_ev[i + 1]) for i in range(args.steps)]
     scan_ms = statistics.mean(b.elapsed_time(e) for b, e in scan_ev)
     total_ms = max_over_ranks(total_ms, world)
     value = Q * world * args.steps / (total_ms / 1e3)
 
-    # end to end through the C ABI from pinned host memory
-    h_q_off = torch.from_numpy(w.q_off.view(np.int32)).pin_memory()
-    h_q_kw = torch.from_numpy(w.q_kw.view(np.int32)).pin_memory()
-    h_ids = torch.empty(Q * K, dtype=torch.int32).pin_memory()
-    h_counts = torch.empty(Q * K, dtype=torch.int32).pin_memory()
-    h_nv = torch.empty(Q, dtype=torch.int32).pin_memory()
-    e_q_off = torch.empty_like(d_q_off)
-    e_q_kw = torch.empty_like(d_q_kw)
+    # end to end through the C ABI: pinned host queries in, host results out,
+    # one genie_search_host call per batch (it returns when the results are
+    # in host memory)
+    import torch as _t
+    h_q_off = _t.from_numpy(w.q_off.view(np.int32)).pin_memory()
+    h_q_kw = _t.from_numpy(w.q_kw.view(np.int32)).pin_memory()
+    h_ids = _t.empty(Q * K, dtype=_t.int32).pin_memory()
+    h_counts = _t.empty(Q * K, dtype=_t.int32).pin_memory()
+    h_nv = _t.empty(Q, dtype=_t.int32).pin_memory()
 
     def e2e_step():
-        e_q_off.copy_(h_q_off, non_blocking=True)
-        e_q_kw.copy_(h_q_kw, non_blocking=True)
-        qs = genie.genie_make_queries(idx, e_q_off, e_q_kw, Q, stream)
-        genie.genie_search(idx, qs, K, out.ids, out.counts, out.n_valid, stream=stream)
-        h_ids.copy_(out.ids, non_blocking=True)
-        h_counts.copy_(out.counts, non_blocking=True)
-        h_nv.copy_(out.n_valid, non_blocking=True)
+        genie.genie_search_host(idx, h_q_off, h_q_kw, Q, K, h_ids, h_counts, h_nv, stream=stream)
 
     for _ in range(max(3, args.warmup)):
         e2e_step()
-    torch.cuda.synchronize()
     barrier(world)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    e2e_lat = []
+    t_e0 = time.perf_counter()
     for _ in range(args.steps):
+        t1 = time.perf_counter()
         e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
+        e2e_lat.append((time.perf_counter() - t1) * 1e3)
+    e2e_ms = max_over_ranks((time.perf_counter() - t_e0) * 1e3, world)
     barrier(world)
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
     h2d = (Q + 1) * 4 + int(w.q_off[-1]) * 4
     d2h = 2 * Q * K * 4 + Q * 4
+    e2e_same = bool(np.array_equal(h_ids.numpy().view(np.uint32).reshape(Q, K), res["ids"]) and
+                    np.array_equal(h_nv.numpy().view(np.uint32), res["n_valid"]))
 
-    # the same batch with the Gate idle (count, then select from the counters):
-    # the on-chip form of the paper's GEN-SPQ comparison, timed after the run
-    ng_opts = genie.make_opts(flags=genie.GENIE_SEARCH_NO_GATE)
-
-    def step_no_gate():
-        qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
-        genie.genie_search(idx, qs, K, out.ids, out.counts, out.n_valid, opts=ng_opts,
-                           stream=stream)
-
-    step_no_gate()
-    ng_ms, _ = timed_steps(step_no_gate, max(3, args.steps // 3), stream)
-    ng_ms /= max(3, args.steps // 3)
     cal = genie.genie_calibrate()
-
-    # c-PQ counters from one more (untimed) pass
-    stats = torch.zeros(8, dtype=torch.int64, device="cuda")
-    qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
-    kernel = genie.genie_search_shape(idx, qs, K).kernel_name()
-    genie.genie_search(idx, qs, K, out.ids, out.counts, out.n_valid,
-                       opts=genie.make_opts(d_stats=stats), stream=stream)
-    st = stats.cpu().numpy()
-    cpq = {"gate_passes_per_posting": float(st[0]) / entries, "ht_inserts": int(st[1]),
-           "blocks": int(st[4]), "blocks_bitmap_fallback": int(st[2]),
-           "blocks_gateless_unseeded": int(st[6]), "bad_ids": int(st[5])}
-    del qs
-
+    cpq = cpq_stats(genie, idx, d_q_off, d_q_kw, Q, K, out, stream, entries)
+    rows = sampled_rows(Q)
+    parity = parity_sampled(w, res, rows) if rank == 0 else None
+    if keep is not None:
+        keep.update(w=w, idx=idx, d_q_off=d_q_off, d_q_kw=d_q_kw, plain_ms=total_ms / args.steps,
+                    plain_res=res)
     if rank != 0:
-        return
-    peak, peak_kind = measured_peaks()
-    algo_bytes = 4.0 * entries  # one 4-byte object id read per posting scanned
-    achieved = algo_bytes / (scan_ms / 1e3) / 1e9
+        return None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": config_dict(w, world, entries),
+        "config": config_dict(w, world),
+        "entries_per_step": int(entries),
         "entries_per_s": entries * world * args.steps / (total_ms / 1e3),
         "latency_ms": {"batch_p50": float(np.percentile(per_step, 50)),
-                       "batch_p99": float(np.percentile(per_step, 99))},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic_from_profile(),
-                     "kernel": kernel, "peak_kind": peak_kind + " hbm_gbs",
-                     "scan_ms": scan_ms, "algorithmic_bytes_per_launch": algo_bytes},
-        "smem_atomic_roofline": {
-            "bound": "shared-memory atomic adds (one per posting)",
-            "achieved": entries / (scan_ms / 1e3), "peak": cal.smem_atomics_per_s,
-            "unit": "updates/s", "frac": entries / (scan_ms / 1e3) / cal.smem_atomics_per_s,
-            "peak_kind": "measured by genie_calibrate on this GPU"},
-        "ablation_no_gate": {"ms_per_step": ng_ms, "value": Q * world / (ng_ms / 1e3),
-                             "c_pq_vs_no_gate": ng_ms / (total_ms / args.steps)},
+                       "batch_p99": float(np.percentile(per_step, 99)),
+                       "e2e_batch_p50": float(np.percentile(e2e_lat, 50)),
+                       "e2e_batch_p99": float(np.percentile(e2e_lat, 99))},
+        "roofline": scan_roofline(entries, scan_ms, kernel, traffic_from_profile()),
+        "smem_atomic_roofline": atomic_roofline(entries, scan_ms, cal),
         "e2e": {"value": Q * world * args.steps / (e2e_ms / 1e3), "unit": UNIT,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "api": "genie_search_host (synchronous: each batch's copies, compile, search "
+                       "and copy-back complete before the next call)",
+                "results_equal_device_path": e2e_same},
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
         "cpq": cpq,
+        "parity_sampled": {"queries": [int(r) for r in rows], "ok": bool(parity)},
+        "index_build_s": build_s,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, CPU_SAMPLE)
+    return line
+
+
+def cpu_baseline(w, n_sample: int) -> dict:
+    import oracle
+    sub = w.subset(np.arange(n_sample))
+    oracle.topk(sub.subset(np.arange(2)))  # load and warm
+    t0 = time.perf_counter()
+    oracle.topk(sub)
+    dt = time.perf_counter() - t0
+    return {"value": n_sample / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "first %d of the %d queries, brute force over all %d objects "
+                      "(%.1f s wall)" % (n_sample, w.n_queries, w.n_objects, dt)}
+
+
+def run_reference(args, rank, world):
+    """The oracle on a bounded sample of the headline batch, on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    w = headline_workload(0, 1)
+    sub = w.subset(np.arange(REF_SAMPLE))
+    oracle.topk(sub.subset(np.arange(2)))
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.topk(sub)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    step_s = sum(times) / len(times)
+    value = REF_SAMPLE / step_s
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "impl": "reference",
+            "config": config_dict(w, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(),
+                             "kind": "oracle",
+                             "sample": "%d queries per step (first %d of %d), brute force over "
+                                       "%d objects" % (REF_SAMPLE, REF_SAMPLE, w.n_queries,
+                                                       w.n_objects)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def timed_steps(step, steps, stream):
-    """CUDA-event time of `steps` calls of step(); returns (total ms, per-step ms)."""
-    import torch
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
-    torch.cuda.synchronize()
-    ev[0].record(stream)
-    for i in range(steps):
-        step()
-        ev[i + 1].record(stream)
-    torch.cuda.synchronize()
-    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
-    return ev[0].elapsed_time(ev[-1]), per
+def leg_steps(args) -> int:
+    return max(3, min(args.steps, 10))
 
 
-def run_learned(args, rank, world, local):
-    """Plain vs learned-seed search on the 4M-object LSH workload."""
+def leg_lsh1m(args):
+    """C2: 1,000,000 LSH objects, 1024 queries, k = 100 (plain path), with the
+    gateless ablation (count, then select from the counters) beside it."""
     import torch
     import synth
-    from paper_1603_08390_gb300 import _build, genie, learned, runner
+    from paper_1603_08390_gb300 import genie, runner
 
-    _build.build()
-    torch.cuda.set_device(local)
     k = 100
-    w = synth.config(4)
+    w = synth.config(2)
     idx = runner.build_index(w)
+    Q = w.n_queries
+    d_q_off, d_q_kw = runner.to_dev(w.q_off), runner.to_dev(w.q_kw)
+    out = runner.Outputs(Q, k)
+    stream = torch.cuda.current_stream()
+    steps = leg_steps(args)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for b, e in ev:
+        b.record(stream)
+        e.record(stream)
+    it = iter(range(10 ** 9))
+
+    def step():
+        i = next(it)
+        opts = genie.make_opts(scan_events=ev[i - W0]) if i >= W0 else None
+        return search_step(genie, idx, d_q_off, d_q_kw, Q, k, out, stream, opts=opts)
+
+    W0 = 3
+    for _ in range(W0):
+        qs = step()
+    entries = qs.n_entries
+    kernel = genie.genie_search_shape(idx, qs, k).kernel_name()
+    del qs
+    ms, per = timed_steps(step, steps, stream)
+    scan_ms = statistics.mean(b.elapsed_time(e) for b, e in ev)
+    res = out.host()
+    ng = genie.make_opts(flags=genie.GENIE_SEARCH_NO_GATE)
+    step_ng = lambda: search_step(genie, idx, d_q_off, d_q_kw, Q, k, out, stream, opts=ng)
+    step_ng()
+    ng_ms, _ = timed_steps(step_ng, steps, stream)
+    res_ng = out.host()
+    cal = genie.genie_calibrate()
+    return {"config": config_dict(w, 1, "lsh-1m: 1,000,000 objects x 256 p-stable LSH keywords, "
+                                        "1024 queries, k=100", k),
+            "value": Q * steps / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
+            "entries_per_step": int(entries), "entries_per_s": entries * steps / (ms / 1e3),
+            "latency_ms": {"batch_p50": float(np.percentile(per, 50)),
+                           "batch_p99": float(np.percentile(per, 99))},
+            "roofline": scan_roofline(entries, scan_ms, kernel,
+                                      traffic_from_profile("scan_cpq_lsh1m_ncu.md")),
+            "smem_atomic_roofline": atomic_roofline(entries, scan_ms, cal),
+            "cpq": cpq_stats(genie, idx, d_q_off, d_q_kw, Q, k, out, stream, entries),
+            "ablation_no_gate": {"ms_per_step": ng_ms / steps, "value": Q * steps / (ng_ms / 1e3),
+                                 "c_pq_speedup": ng_ms / ms,
+                                 "identical_results": all(np.array_equal(res[x], res_ng[x])
+                                                          for x in res)},
+            "parity_sampled": {"ok": parity_sampled(w, res, sampled_rows(Q))},
+            "gpu_launches": 3 * steps}
+
+
+def leg_learned(args, keep):
+    """C4 learned threshold on the headline batch: a 64-128-1 network trained
+    on the GPU predicts each query's k-th count and seeds the AuditThreshold;
+    plain vs seeded, plus the ceiling of any predictor (seeds = the exact
+    k-th counts the plain search returned)."""
+    import torch
+    import synth
+    from paper_1603_08390_gb300 import genie, learned, runner
+
+    k = K
+    w, idx = keep["w"], keep["idx"]
+    d_q_off, d_q_kw = keep["d_q_off"], keep["d_q_kw"]
+    Q = w.n_queries
+    stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
     tq_off, tq_kw = synth.lsh_training_queries(100_000, config=4)
     tr = learned.train_predictor(idx, tq_off, tq_kw, k, epochs=20, batch=256, lr=2e-3)
     train_s = time.perf_counter() - t0
-    Q = w.n_queries
-    d_q_off, d_q_kw = runner.to_dev(w.q_off), runner.to_dev(w.q_kw)
-    stream = torch.cuda.current_stream()
-    out_p, out_l = runner.Outputs(Q, k), runner.Outputs(Q, k)
+    out_p, out_l, out_c = runner.Outputs(Q, k), runner.Outputs(Q, k), runner.Outputs(Q, k)
     seeds = torch.empty(Q, dtype=torch.int32, device="cuda")
 
     def plain():
-        qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
-        genie.genie_search(idx, qs, k, out_p.ids, out_p.counts, out_p.n_valid, stream=stream)
+        search_step(genie, idx, d_q_off, d_q_kw, Q, k, out_p, stream)
 
     def seeded(stats=None):
         qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
@@ -457,200 +580,68 @@ def run_learned(args, rank, world, local):
         genie.genie_search(idx, qs, k, out_l.ids, out_l.counts, out_l.n_valid,
                            opts=genie.make_opts(d_seed=seeds, d_stats=stats), stream=stream)
 
-    for _ in range(args.warmup):
+    plain()
+    torch.cuda.synchronize()
+    # the best any predictor can do: seed each query with its exact k-th count
+    exact = out_p.counts.view(Q, k)[:, k - 1].clone().clamp_(min=1)
+
+    def ceiling(stats=None):
+        search_step(genie, idx, d_q_off, d_q_kw, Q, k, out_c, stream,
+                    opts=genie.make_opts(d_seed=exact, d_stats=stats))
+
+    steps = leg_steps(args)
+    for _ in range(2):
         plain()
         seeded()
-    clocks = Clocks(torch.cuda.current_device())
-    clocks.start()
-    clocks.mark_begin()
-    p_ms, _ = timed_steps(plain, args.steps, stream)
-    l_ms, per = timed_steps(seeded, args.steps, stream)
-    clocks.mark_end()
-    clk = clocks.stop()
-    st_p = torch.zeros(8, dtype=torch.int64, device="cuda")
-    st_l = torch.zeros(8, dtype=torch.int64, device="cuda")
-    qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
-    genie.genie_search(idx, qs, k, out_p.ids, out_p.counts, out_p.n_valid,
-                       opts=genie.make_opts(d_stats=st_p), stream=stream)
-    seeded(st_l)
-    a, b = out_p.host(), out_l.host()
-    identical = all(np.array_equal(a[key], b[key]) for key in a)
-    sp, sl = st_p.cpu().numpy(), st_l.cpu().numpy()
-    entries = qs.n_entries
-    line = {
-        "metric": METRIC, "value": Q * args.steps / (l_ms / 1e3), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": l_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic", "impl": "genie-learned",
-        "config": {"workload": "lsh-4m learned threshold: 4,000,000 objects x 256 LSH keywords, "
-                               "4096 queries, k=100; 64-128-1 bf16 MLP trained on 100k query / "
-                               "k-th-count pairs from the plain search",
-                   "n_objects": w.n_objects, "n_queries": Q, "k": k, "entries_per_step": int(entries)},
-        "plain": {"value": Q * args.steps / (p_ms / 1e3), "ms_per_step": p_ms / args.steps,
-                  "gate_passes": int(sp[0]), "ht_inserts": int(sp[1])},
-        "learned": {"value": Q * args.steps / (l_ms / 1e3), "ms_per_step": l_ms / args.steps,
-                    "gate_passes": int(sl[0]), "ht_inserts": int(sl[1]),
-                    "reruns": int(sl[3]), "rerun_rate": float(sl[3]) / Q,
-                    "batch_p50_ms": float(np.percentile(per, 50)),
-                    "batch_p99_ms": float(np.percentile(per, 99))},
-        "speedup_vs_plain": p_ms / l_ms, "identical_results": bool(identical),
-        "training": {"seconds": train_s, "train_loss": tr["train_loss"], "margin": tr["margin"],
-                     "n_train": tr["n_train"], "n_val": tr["n_val"],
-                     "target_mean": tr["target_mean"]},
-        "entries_per_s": entries * args.steps / (l_ms / 1e3),
-        "gpu_launches": 5 * args.steps,
-        "clocks": clk,
-    }
-    print(json.dumps(line), flush=True)
+        ceiling()
+    p_ms, _ = timed_steps(plain, steps, stream)
+    l_ms, per = timed_steps(seeded, steps, stream)
+    c_ms, _ = timed_steps(ceiling, steps, stream)
+    st = {}
+    for name, fn in (("plain", None), ("learned", seeded), ("ceiling", ceiling)):
+        s = torch.zeros(8, dtype=torch.int64, device="cuda")
+        if fn is None:
+            search_step(genie, idx, d_q_off, d_q_kw, Q, k, out_p, stream,
+                        opts=genie.make_opts(d_stats=s))
+        else:
+            fn(s)
+        st[name] = s.cpu().numpy()
+    a, b, c = out_p.host(), out_l.host(), out_c.host()
+    same = all(np.array_equal(a[x], b[x]) and np.array_equal(a[x], c[x]) for x in a)
+    return {"config": {"workload": "lsh-4m learned threshold: the headline batch; 64-128-1 bf16 "
+                                   "MLP trained on the GPU on 100k query / k-th-count pairs "
+                                   "from the plain search", "n_queries": Q, "k": k},
+            "plain": {"value": Q * steps / (p_ms / 1e3), "ms_per_step": p_ms / steps,
+                      "gate_passes": int(st["plain"][0]), "ht_inserts": int(st["plain"][1])},
+            "learned": {"value": Q * steps / (l_ms / 1e3), "ms_per_step": l_ms / steps,
+                        "gate_passes": int(st["learned"][0]), "ht_inserts": int(st["learned"][1]),
+                        "reruns": int(st["learned"][3]), "rerun_rate": float(st["learned"][3]) / Q,
+                        "batch_p50_ms": float(np.percentile(per, 50)),
+                        "batch_p99_ms": float(np.percentile(per, 99))},
+            "ceiling_exact_seeds": {"value": Q * steps / (c_ms / 1e3), "ms_per_step": c_ms / steps,
+                                    "gate_passes": int(st["ceiling"][0])},
+            "speedup_vs_plain": p_ms / l_ms, "ceiling_speedup_vs_plain": p_ms / c_ms,
+            "identical_results": bool(same),
+            "training": {"seconds": train_s, "train_loss": tr["train_loss"],
+                         "margin": tr["margin"], "n_train": tr["n_train"], "n_val": tr["n_val"],
+                         "target_mean": tr["target_mean"]},
+            "parity_sampled": {"ok": parity_sampled(w, b, sampled_rows(Q))},
+            "gpu_launches": 5 * steps}
 
 
-def run_parts(args, rank, world, local):
-    """Multiple loadings (Sec. 3.4): the 4M-object LSH objects as four parts of
-    1M held in pinned host memory, 1024 queries per batch, against one
-    device-resident index of the same objects."""
+def leg_batched(args):
+    """C3: 4M Zipf(1.1) sets, 8192 queries of 8-512 keywords, k = 10: plain
+    launches vs the persistent, graph-captured, autotuned batch."""
     import torch
     import synth
-    from paper_1603_08390_gb300 import _build, genie, runner
+    from paper_1603_08390_gb300 import genie, runner
 
-    _build.build()
-    torch.cuda.set_device(local)
-    k, P = 100, 4
-    w = synth.config(4).subset(np.arange(N_QUERIES))
-    N, Q = w.n_objects, w.n_queries
-    parts = runner.build_parts(w, [(p * N // P, (p + 1) * N // P) for p in range(P)])
-    info = parts.info
-    idx = runner.build_index(w)
-    d_q_off, d_q_kw = runner.to_dev(w.q_off), runner.to_dev(w.q_kw)
-    stream = torch.cuda.current_stream()
-    out_p, out_d = runner.Outputs(Q, k), runner.Outputs(Q, k)
-
-    def step_parts():
-        parts.search(d_q_off, d_q_kw, Q, k, out_p.ids, out_p.counts, out_p.n_valid, stream=stream)
-
-    def step_device():
-        qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
-        genie.genie_search(idx, qs, k, out_d.ids, out_d.counts, out_d.n_valid, stream=stream)
-
-    for _ in range(max(3, args.warmup)):
-        step_parts()
-        step_device()
-    torch.cuda.synchronize()
-    clocks = Clocks(torch.cuda.current_device())
-    clocks.start()
-    clocks.mark_begin()
-    p_ms, per = timed_steps(step_parts, args.steps, stream)
-    d_ms, _ = timed_steps(step_device, args.steps, stream)
-    clocks.mark_end()
-    clk = clocks.stop()
-    a, b = out_p.host(), out_d.host()
-    identical = all(np.array_equal(a[key], b[key]) for key in a)
-    qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
-    entries = qs.n_entries
-    line = {
-        "metric": METRIC, "value": Q * args.steps / (p_ms / 1e3), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": p_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic", "impl": "genie-parts",
-        "config": {"workload": "lsh-4m multiple loadings: the 4,000,000 LSH objects (256 keywords "
-                               "each) as 4 index parts of 1,000,000 in pinned host memory, copied "
-                               "to the device part by part during each batch; 1024 queries, k=100",
-                   "n_objects": N, "n_queries": Q, "k": k, "parts": P,
-                   "entries_per_step": int(entries)},
-        "h2d_bytes_per_step": int(info.host_bytes),
-        "h2d_gb_per_s": info.host_bytes * args.steps / (p_ms / 1e3) / 1e9,
-        "device_resident": {"value": Q * args.steps / (d_ms / 1e3), "ms_per_step": d_ms / args.steps,
-                            "device_index_bytes": int(idx.device_bytes)},
-        "parts_vs_device_resident": d_ms / p_ms, "identical_results": bool(identical),
-        "latency_ms": {"batch_p50": float(np.percentile(per, 50)),
-                       "batch_p99": float(np.percentile(per, 99))},
-        "entries_per_s": entries * args.steps / (p_ms / 1e3),
-        "gpu_launches": (4 * P + 2) * args.steps,
-        "clocks": clk,
-    }
-    print(json.dumps(line), flush=True)
-
-
-def run_seq(args, rank, world, local):
-    """Sequence search by ordered n-grams (Sec. 5.1): 1M sequences of 40-100
-    characters, 1024 queries with 1-6 edits, K = 128 candidates, k = 1."""
-    import torch
-    import synth
-    from paper_1603_08390_gb300 import _build, runner
-
-    _build.build()
-    torch.cuda.set_device(local)
-    n, R, K, k = 3, 32, 128, 1
-    seqs = synth.sequences(1_000_000, (40, 100), 26, N_QUERIES, (1, 6), config=6)
-    si = runner.SeqIndex(seqs.s_off, seqs.s_chars, n, seqs.sigma, R)
-    Q = seqs.n_queries
-    d_q = (runner.to_dev(seqs.q_off), runner.to_dev(seqs.q_chars))
-    out = runner.SeqOutputs(Q, K, k)
-    stream = torch.cuda.current_stream()
-
-    def step():
-        runner.sa_search(si, seqs.q_off, seqs.q_chars, K, k, out=out, stream=stream, d_q=d_q)
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    clocks = Clocks(torch.cuda.current_device())
-    clocks.start()
-    clocks.mark_begin()
-    ms, per = timed_steps(step, args.steps, stream)
-    clocks.mark_end()
-    clk = clocks.stop()
-    res = out.host()
-    line = {
-        "metric": METRIC, "value": Q * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic", "impl": "genie-sequences",
-        "config": {"workload": "seq-1m: 1,000,000 sequences of 40-100 characters over 26 letters "
-                               "(Zipf(1) frequencies), ordered 3-grams; 1024 queries, each a data "
-                               "sequence with 1-6 random edits; top-128 candidates by match count, "
-                               "verified by edit distance (k=1)",
-                   "n_sequences": seqs.n_seqs, "n_queries": Q, "n": n, "K": K, "k": k},
-        "certified_fraction": float(res["certified"].mean()),
-        "examined_mean": float(res["examined"].mean()),
-        "latency_ms": {"batch_p50": float(np.percentile(per, 50)),
-                       "batch_p99": float(np.percentile(per, 99))},
-        "gpu_launches": 7 * args.steps,
-        "clocks": clk,
-    }
-    if not args.no_cpu_baseline:
-        import oracle
-        from oracle import sa
-        n_s = 16
-        sub = seqs.subset(np.arange(n_s))
-        t0 = time.perf_counter()
-        truth = sa.topk_ed(seqs.s_off, seqs.s_chars, sub.q_off, sub.q_chars, k)
-        cpu_s = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": n_s / cpu_s, "unit": UNIT, "cores": oracle.threads(),
-                                "kind": "oracle",
-                                "sample": "%d queries: brute-force edit distance to all 1M sequences"
-                                          % n_s}
-        cert = res["certified"][:n_s]
-        line["sampled_certified_equal_truth"] = bool(np.all(
-            res["ed"][:n_s][cert, 0] == truth["ed"][cert, 0]))
-    print(json.dumps(line), flush=True)
-
-
-def run_batched(args, rank, world, local):
-    """Plain one-launch-per-kernel search vs the persistent, graph-captured,
-    autotuned batch on the 4M-object Zipf-set workload."""
-    import torch
-    import synth
-    from paper_1603_08390_gb300 import _build, genie, runner
-
-    _build.build()
-    torch.cuda.set_device(local)
     k = 10
     w = synth.config(3)
     idx = runner.build_index(w)
     Q = w.n_queries
     d_q_off, d_q_kw = runner.to_dev(w.q_off), runner.to_dev(w.q_kw)
     stream = torch.cuda.current_stream()
-    # autotune on a sample of 512 queries
     sample = w.subset(np.arange(0, Q, Q // 512)[:512])
     sq = runner.compile_queries(idx, sample)
     t0 = time.perf_counter()
@@ -659,99 +650,75 @@ def run_batched(args, rank, world, local):
     qs0 = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
     batch = genie.Batch(idx, Q, qs0.max_bound, k, tuned)
     entries = qs0.n_entries
+    kernel = genie.genie_search_shape(idx, qs0, k).kernel_name()
+    del qs0
     out_p, out_b = runner.Outputs(Q, k), runner.Outputs(Q, k)
-    topt = genie.make_opts(block_shift=tuned.block_shift, threads=tuned.threads,
-                           unroll=tuned.unroll, ht_slots=tuned.ht_slots)
+    steps = max(3, min(args.steps, 4))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for b, e in ev:
+        b.record(stream)
+        e.record(stream)
+    idx_ev = [0]
 
-    def plain():
-        qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
-        genie.genie_search(idx, qs, k, out_p.ids, out_p.counts, out_p.n_valid, stream=stream)
-
-    def plain_tuned():
-        qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
-        genie.genie_search(idx, qs, k, out_p.ids, out_p.counts, out_p.n_valid, opts=topt,
-                           stream=stream)
+    def plain(timed=False):
+        opts = None
+        if timed:
+            opts = genie.make_opts(scan_events=ev[idx_ev[0]])
+            idx_ev[0] += 1
+        search_step(genie, idx, d_q_off, d_q_kw, Q, k, out_p, stream, opts=opts)
 
     def batched():
         qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
         batch.run(qs, out_b.ids, out_b.counts, out_b.n_valid, stream=stream)
 
-    for _ in range(args.warmup):
-        plain()
-        batched()
-    clocks = Clocks(torch.cuda.current_device())
-    clocks.start()
-    clocks.mark_begin()
-    p_ms, _ = timed_steps(plain, args.steps, stream)
-    pt_ms, _ = timed_steps(plain_tuned, args.steps, stream)
-    b_ms, per = timed_steps(batched, args.steps, stream)
-    clocks.mark_end()
-    clk = clocks.stop()
+    plain()
+    batched()
+    p_ms, _ = timed_steps(lambda: plain(True), steps, stream)
+    b_ms, per = timed_steps(batched, steps, stream)
+    scan_ms = statistics.mean(b.elapsed_time(e) for b, e in ev)
     a, b = out_p.host(), out_b.host()
-    identical = all(np.array_equal(a[key], b[key]) for key in a)
-    rows = np.arange(0, Q, Q // 8)[:8]
-    import oracle
-    ref = oracle.topk(w.subset(rows))
-    sampled_ok = all(np.array_equal(b["ids"][q, :int(ref["n_valid"][j])],
-                                    ref["ids"][j, :int(ref["n_valid"][j])]) and
-                     b["n_valid"][q] == ref["n_valid"][j] for j, q in enumerate(rows))
-    line = {
-        "metric": METRIC, "value": Q * args.steps / (b_ms / 1e3), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": b_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic", "impl": "genie-batched",
-        "config": {"workload": "sets-4m batched: 4,000,000 Zipf(1.1) keyword sets of 16-256 over "
-                               "a 2^20 vocabulary, 8192 queries of 8-512 keywords, k=10; one "
-                               "persistent CUDA-graph launch per batch, autotuned shape",
-                   "n_objects": w.n_objects, "n_queries": Q, "k": k, "entries_per_step": int(entries)},
-        "plain_default": {"value": Q * args.steps / (p_ms / 1e3), "ms_per_step": p_ms / args.steps},
-        "plain_tuned": {"value": Q * args.steps / (pt_ms / 1e3), "ms_per_step": pt_ms / args.steps},
-        "batched": {"value": Q * args.steps / (b_ms / 1e3), "ms_per_step": b_ms / args.steps,
-                    "batch_p50_ms": float(np.percentile(per, 50)),
-                    "batch_p99_ms": float(np.percentile(per, 99))},
-        "autotune": {"block_shift": tuned.block_shift, "threads": tuned.threads,
-                     "unroll": tuned.unroll, "ht_slots": tuned.ht_slots,
-                     "sample_ms": tuned.tuned_ms, "seconds": tune_s,
-                     "from_cache": bool(tuned.from_cache)},
-        "speedup_vs_plain_default": p_ms / b_ms, "identical_results": bool(identical),
-        "oracle_sampled_queries_ok": bool(sampled_ok),
-        "entries_per_s": entries * args.steps / (b_ms / 1e3),
-        "roofline": {"bound": "hbm", "achieved": 4.0 * entries / (b_ms / args.steps / 1e3) / 1e9,
-                     "peak": measured_peaks()[0], "unit": "GB/s",
-                     "frac": 4.0 * entries / (b_ms / args.steps / 1e3) / 1e9 / measured_peaks()[0],
-                     "traffic": None, "kernel": "batch_cpq_kernel (whole step)"},
-        "gpu_launches": 3 * args.steps,
-        "clocks": clk,
-    }
-    print(json.dumps(line), flush=True)
+    identical = all(np.array_equal(a[x], b[x]) for x in a)
+    cal = genie.genie_calibrate()
+    return {"config": config_dict(w, 1, "sets-4m batched: 4,000,000 Zipf(1.1) keyword sets of "
+                                        "16-256 over a 2^20 vocabulary, 8192 queries of 8-512 "
+                                        "keywords, k=10", k),
+            "value": Q * steps / (b_ms / 1e3), "ms_per_step": b_ms / steps, "steps": steps,
+            "entries_per_step": int(entries), "entries_per_s": entries * steps / (b_ms / 1e3),
+            "plain": {"value": Q * steps / (p_ms / 1e3), "ms_per_step": p_ms / steps,
+                      "kernel": kernel, "scan_ms": scan_ms,
+                      "roofline": scan_roofline(entries, scan_ms, kernel),
+                      "smem_atomic_roofline": atomic_roofline(entries, scan_ms, cal)},
+            "batched": {"value": Q * steps / (b_ms / 1e3), "ms_per_step": b_ms / steps,
+                        "batch_p50_ms": float(np.percentile(per, 50)),
+                        "batch_p99_ms": float(np.percentile(per, 99))},
+            "autotune": {"block_shift": tuned.block_shift, "threads": tuned.threads,
+                         "unroll": tuned.unroll, "ht_slots": tuned.ht_slots,
+                         "sample_ms": tuned.tuned_ms, "seconds": tune_s,
+                         "from_cache": bool(tuned.from_cache)},
+            "batched_speedup_vs_plain": p_ms / b_ms, "identical_results": bool(identical),
+            "parity_sampled": {"ok": parity_sampled(w, b, sampled_rows(Q))},
+            "gpu_launches": 5 * steps}
 
 
-def run_serving(args, rank, world, local):
-    """Continuous-batching server: saturation throughput and p50/p99 latency
-    under Poisson arrivals at fractions of it (8M x 64 Zipf sets)."""
+def leg_serving(args):
+    """C5: continuous-batching server on 8M x 64 Zipf sets; saturation and
+    p50/p99 latency under Poisson arrivals at fractions of it."""
     import torch
     import synth
-    from paper_1603_08390_gb300 import _build, genie, runner
+    from paper_1603_08390_gb300 import genie, runner
 
-    _build.build()
-    torch.cuda.set_device(local)
     w = synth.sets(8_000_000, (64, 64), 1 << 22, 16, (8, 512), 10, config=5)  # the objects
     idx = runner.build_index(w)
     n_req = 4000
     q_off, q_kw, ks, _ = synth.serving_requests(n_req, 1.0, config=5)
-    budget = 512 * w.n_objects  # counter bytes of 512 queries at 8 bits per object
-    opts = genie.ServerOpts(bc_budget_bytes=budget, bits_per_object=8, max_batch=256,
-                            max_query_keywords=512, k_max=100, streams=2)
+    opts = genie.ServerOpts(max_batch=256, max_query_keywords=512, k_max=100, streams=2)
     srv = genie.Server(idx, opts)
-    # warm-up, then saturation: every request at t = 0
     srv.replay(q_off[:201] - q_off[0], q_kw[:q_off[200]], ks[:200], np.zeros(200))
     t0 = time.perf_counter()
-    lat0, ids0, _, nv0 = srv.replay(q_off, q_kw, ks, np.zeros(n_req))
+    lat0, ids0, cnt0, nv0 = srv.replay(q_off, q_kw, ks, np.zeros(n_req))
     sat_s = time.perf_counter() - t0
     sat_qps = n_req / sat_s
-    clocks = Clocks(torch.cuda.current_device())
-    clocks.start()
-    clocks.mark_begin()
     sweep = []
     rng = np.random.default_rng(123)
     for frac in (0.25, 0.5, 0.75, 0.9):
@@ -766,30 +733,228 @@ def run_serving(args, rank, world, local):
                       "p50_ms": float(np.percentile(lat, 50) * 1e3),
                       "p99_ms": float(np.percentile(lat, 99) * 1e3),
                       "mean_ms": float(lat.mean() * 1e3), "results_same_as_saturation": same})
-    clocks.mark_end()
-    clk = clocks.stop()
     st = srv.stats()
-    qsz = np.diff(q_off.astype(np.int64))
-    line = {
-        "metric": METRIC, "value": sat_qps, "unit": UNIT, "n_gpus": 1, "steps": len(sweep) + 1,
-        "warmup": 1, "ms_per_step": sat_s * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32", "data": "synthetic", "impl": "genie-serving",
-        "config": {"workload": "serving: 8,000,000 objects x 64 Zipf(1.1) keywords over 2^22, "
-                               "requests of 8-512 keywords, k uniform in {1, 10, 100}, Poisson "
-                               "arrivals; admission by Bitmap-Counter bytes (8 bits per object "
-                               "per query), budget = 512 queries",
-                   "n_objects": w.n_objects, "n_requests": n_req,
-                   "mean_request_keywords": float(qsz.mean()), "streams": 2, "max_batch": 256},
-        "saturation": {"qps": sat_qps, "p50_ms": float(np.percentile(lat0, 50) * 1e3),
-                       "p99_ms": float(np.percentile(lat0, 99) * 1e3)},
-        "sweep": sweep,
-        "server": {"launches": int(st.launches), "queries": int(st.queries),
-                   "mean_batch": float(st.queries) / max(1, st.launches),
-                   "deferred_admissions": int(st.deferred_admissions),
-                   "max_queries_in_flight": int(st.max_queries_in_flight)},
-        "clocks": clk,
-    }
     srv.close()
+    # oracle check of sampled requests against the same objects
+    rows = sampled_rows(n_req)
+    wq = synth.Workload(name="serving-requests", kind="keywords", n_objects=w.n_objects,
+                        vocab=w.vocab, obj_off=w.obj_off,
+                        obj_kw=w.obj_kw, n_queries=n_req, q_off=q_off, q_kw=q_kw,
+                        k=np.asarray(ks, dtype=np.uint32))
+    res = {"ids": ids0, "counts": cnt0, "n_valid": nv0}
+    qsz = np.diff(q_off.astype(np.int64))
+    # the plain search on the same requests (one batch, k = 100) for comparison
+    d_q_off, d_q_kw = runner.to_dev(q_off), runner.to_dev(q_kw)
+    out = runner.Outputs(n_req, 100)
+    stream = torch.cuda.current_stream()
+    d_k = runner.to_dev(np.asarray(ks, dtype=np.uint32))
+    fn = lambda: search_step(genie, idx, d_q_off, d_q_kw, n_req, 100, out, stream, d_k=d_k)
+    fn()
+    pl_ms, _ = timed_steps(fn, 3, stream)
+    return {"config": {"workload": "serving: 8,000,000 objects x 64 Zipf(1.1) keywords over 2^22, "
+                                   "requests of 8-512 keywords, k uniform in {1, 10, 100}, Poisson "
+                                   "arrivals; admission by the device memory a request holds",
+                       "n_objects": w.n_objects, "n_requests": n_req,
+                       "mean_request_keywords": float(qsz.mean()), "streams": 2, "max_batch": 256},
+            "value": sat_qps,
+            "saturation": {"qps": sat_qps, "p50_ms": float(np.percentile(lat0, 50) * 1e3),
+                           "p99_ms": float(np.percentile(lat0, 99) * 1e3)},
+            "sweep": sweep,
+            "plain_one_batch": {"value": n_req * 3 / (pl_ms / 1e3), "ms_per_batch": pl_ms / 3},
+            "server": {"launches": int(st.launches), "queries": int(st.queries),
+                       "mean_batch": float(st.queries) / max(1, st.launches),
+                       "deferred_admissions": int(st.deferred_admissions),
+                       "max_queries_in_flight": int(st.max_queries_in_flight)},
+            "parity_sampled": {"ok": parity_sampled(wq, res, rows)}}
+
+
+def leg_parts(args, keep):
+    """Multiple loadings (Sec. 3.4): the headline objects as four index parts
+    of 1M in pinned host memory, copied to the device part by part during each
+    batch of 1024 queries, against the device-resident index."""
+    import torch
+    from paper_1603_08390_gb300 import genie, runner
+
+    k, P = K, 4
+    w = keep["w"].subset(np.arange(1024))
+    idx = keep["idx"]
+    N, Q = w.n_objects, w.n_queries
+    parts = runner.build_parts(w, [(p * N // P, (p + 1) * N // P) for p in range(P)])
+    info = parts.info
+    d_q_off, d_q_kw = runner.to_dev(w.q_off), runner.to_dev(w.q_kw)
+    stream = torch.cuda.current_stream()
+    out_p, out_d = runner.Outputs(Q, k), runner.Outputs(Q, k)
+
+    def step_parts():
+        parts.search(d_q_off, d_q_kw, Q, k, out_p.ids, out_p.counts, out_p.n_valid, stream=stream)
+
+    def step_device():
+        search_step(genie, idx, d_q_off, d_q_kw, Q, k, out_d, stream)
+
+    for _ in range(2):
+        step_parts()
+        step_device()
+    steps = leg_steps(args)
+    p_ms, per = timed_steps(step_parts, steps, stream)
+    d_ms, _ = timed_steps(step_device, steps, stream)
+    a, b = out_p.host(), out_d.host()
+    identical = all(np.array_equal(a[x], b[x]) for x in a)
+    res = {"config": {"workload": "lsh-4m multiple loadings: the 4,000,000 LSH objects as 4 index "
+                                  "parts of 1,000,000 in pinned host memory; 1024 queries, k=100",
+                      "n_objects": N, "n_queries": Q, "k": k, "parts": P},
+           "value": Q * steps / (p_ms / 1e3), "ms_per_step": p_ms / steps,
+           "h2d_bytes_per_step": int(info.host_bytes),
+           "h2d_gb_per_s": info.host_bytes * steps / (p_ms / 1e3) / 1e9,
+           "device_resident": {"value": Q * steps / (d_ms / 1e3), "ms_per_step": d_ms / steps,
+                               "device_index_bytes": int(idx.device_bytes)},
+           "parts_vs_device_resident": d_ms / p_ms, "identical_results": bool(identical),
+           "latency_ms": {"batch_p50": float(np.percentile(per, 50)),
+                          "batch_p99": float(np.percentile(per, 99))},
+           "gpu_launches": (4 * P + 2) * steps}
+    del parts
+    return res
+
+
+def leg_relational(args):
+    """C1: 10,000 x 16 relational tuples, 64 range queries of 16 items, k = 10."""
+    import torch
+    import synth
+    from paper_1603_08390_gb300 import genie, runner
+
+    w = synth.config(1)
+    idx = runner.build_index(w)
+    stream = torch.cuda.current_stream()
+    args_ = (runner.to_dev(w.item_off), runner.to_dev(w.item_dim), runner.to_dev(w.item_lo),
+             runner.to_dev(w.item_hi))
+    k = int(w.k)
+    out = runner.Outputs(w.n_queries, k)
+
+    def step():
+        qs = genie.genie_compile_ranges(idx, w.values_per_dim, *args_, w.n_queries, stream)
+        genie.genie_search(idx, qs, k, out.ids, out.counts, out.n_valid, stream=stream)
+
+    for _ in range(3):
+        step()
+    steps = leg_steps(args)
+    ms, per = timed_steps(step, steps, stream)
+    res = out.host()
+    import oracle
+    ref = oracle.topk(w)
+    ok = all(np.array_equal(res[x], ref[x]) for x in ("ids", "counts", "n_valid"))
+    return {"config": {"workload": "relational: 10,000 objects x 16 attributes in [0, 64), 64 "
+                                   "queries of 16 range items [v-2, v+2], k=10",
+                       "n_objects": w.n_objects, "n_queries": w.n_queries, "k": k},
+            "value": w.n_queries * steps / (ms / 1e3), "ms_per_step": ms / steps,
+            "latency_ms": {"batch_p50": float(np.percentile(per, 50)),
+                           "batch_p99": float(np.percentile(per, 99))},
+            "parity_all_queries": {"ok": bool(ok)}, "gpu_launches": 3 * steps}
+
+
+def leg_seq(args):
+    """Sequence search by ordered n-grams (Sec. 5.1): 1M sequences of 40-100
+    characters, 1024 queries with 1-6 edits, K = 128 candidates, k = 1."""
+    import torch
+    import synth
+    from paper_1603_08390_gb300 import runner
+
+    n, R, Kc, k = 3, 32, 128, 1
+    seqs = synth.sequences(1_000_000, (40, 100), 26, 1024, (1, 6), config=6)
+    si = runner.SeqIndex(seqs.s_off, seqs.s_chars, n, seqs.sigma, R)
+    Q = seqs.n_queries
+    d_q = (runner.to_dev(seqs.q_off), runner.to_dev(seqs.q_chars))
+    out = runner.SeqOutputs(Q, Kc, k)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        runner.sa_search(si, seqs.q_off, seqs.q_chars, Kc, k, out=out, stream=stream, d_q=d_q)
+
+    for _ in range(3):
+        step()
+    steps = leg_steps(args)
+    ms, per = timed_steps(step, steps, stream)
+    res = out.host()
+    from oracle import sa
+    n_s = 4
+    sub = seqs.subset(np.arange(n_s))
+    truth = sa.topk_ed(seqs.s_off, seqs.s_chars, sub.q_off, sub.q_chars, k)
+    cert = res["certified"][:n_s]
+    return {"config": {"workload": "seq-1m: 1,000,000 sequences of 40-100 characters over 26 "
+                                   "letters, ordered 3-grams; 1024 queries with 1-6 random edits; "
+                                   "top-128 candidates verified by edit distance (k=1)",
+                       "n_sequences": seqs.n_seqs, "n_queries": Q, "n": n, "K": Kc, "k": k},
+            "value": Q * steps / (ms / 1e3), "ms_per_step": ms / steps,
+            "certified_fraction": float(res["certified"].mean()),
+            "examined_mean": float(res["examined"].mean()),
+            "latency_ms": {"batch_p50": float(np.percentile(per, 50)),
+                           "batch_p99": float(np.percentile(per, 99))},
+            "parity_sampled": {"ok": bool(np.all(res["ed"][:n_s][cert, 0] ==
+                                                  truth["ed"][cert, 0])),
+                               "queries": n_s, "certified": int(cert.sum())},
+            "gpu_launches": 7 * steps}
+
+
+LEG_FUNCS = {"lsh1m": leg_lsh1m, "sets4m-batched": leg_batched, "serving": leg_serving,
+             "relational": leg_relational, "seq1m": leg_seq}
+
+
+def run_leg(name, args, keep):
+    import torch
+    t0 = time.perf_counter()
+    try:
+        if name == "lsh4m-learned":
+            r = leg_learned(args, keep)
+        elif name == "lsh4m-parts":
+            r = leg_parts(args, keep)
+        else:
+            r = LEG_FUNCS[name](args)
+    except Exception as e:  # a failed leg is reported, and the others still run
+        r = {"error": "%s: %s" % (type(e).__name__, e)}
+    r["wall_s"] = time.perf_counter() - t0
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return r
+
+
+def run_genie(args, rank, world, local):
+    import torch
+    from paper_1603_08390_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    if args.workload in ("all", "lsh4m"):
+        keep = {}
+        line = run_headline(args, rank, world, local, keep)
+        if rank == 0 and args.workload == "all" and world == 1:
+            legs = {}
+            for name in ("lsh4m-learned", "lsh4m-parts"):  # they reuse the headline index
+                legs[name] = run_leg(name, args, keep)
+            keep.clear()
+            gc.collect()
+            torch.cuda.empty_cache()
+            for name in ("lsh1m", "sets4m-batched", "serving", "relational", "seq1m"):
+                legs[name] = run_leg(name, args, keep)
+            line["legs"] = legs
+            line["suite_wall_s"] = time.perf_counter() - t0
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
+    if rank != 0:
+        return
+    keep = {}
+    if args.workload in ("lsh4m-learned", "lsh4m-parts"):
+        import synth  # noqa: F401
+        from paper_1603_08390_gb300 import runner
+        w = headline_workload(0, 1, args.queries or N_QUERIES)
+        keep.update(w=w, idx=runner.build_index(w), d_q_off=runner.to_dev(w.q_off),
+                    d_q_kw=runner.to_dev(w.q_kw))
+    r = run_leg(args.workload, args, keep)
+    line = {"metric": METRIC, "value": r.get("value"), "unit": UNIT, "n_gpus": 1,
+            "steps": r.get("steps", leg_steps(args)), "warmup": 3,
+            "ms_per_step": r.get("ms_per_step"), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "impl": "genie-" + args.workload,
+            "config": r.get("config", {"workload": args.workload}), "leg": r}
     print(json.dumps(line), flush=True)
 
 
@@ -798,21 +963,6 @@ def main():
     rank, world, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, rank, world)
-    elif args.workload == "lsh4m-learned":
-        if rank == 0:
-            run_learned(args, rank, world, local)
-    elif args.workload == "seq1m":
-        if rank == 0:
-            run_seq(args, rank, world, local)
-    elif args.workload == "lsh4m-parts":
-        if rank == 0:
-            run_parts(args, rank, world, local)
-    elif args.workload == "sets4m-batched":
-        if rank == 0:
-            run_batched(args, rank, world, local)
-    elif args.workload == "serving":
-        if rank == 0:
-            run_serving(args, rank, world, local)
     else:
         run_genie(args, rank, world, local)
     if world > 1:

@@ -274,6 +274,30 @@ typedef struct {
 } genie_search_shape_info;
 
 /*
+ * End-to-end search from host memory: the query transfer, match and select
+ * stages of one batch (Table 2) plus the copy of the results back, in one
+ * call.
+ *   h_q_off [n_queries+1] uint32, HOST, h_q_off[0] = 0; h_q_kw [h_q_off[n]]
+ *              uint32 keywords, HOST: keyword queries as for
+ *              genie_make_queries.  Pinned (page-locked) memory lets the
+ *              copies run at full speed; pageable memory works too.
+ *   n_queries  1 .. 2^24;  k, opts as for genie_search.
+ *   h_k        NULL, or [n_queries] uint32 HOST per-query k_q in 1..k.
+ *   h_ids, h_counts [n_queries * k], h_n_valid [n_queries] uint32: HOST
+ *              outputs, written completely, in genie_search's layout.
+ * The queries are copied to the device on `stream`, compiled, searched, and
+ * the results copied back; the call synchronises `stream` and returns once
+ * the results are in the host buffers.  Device memory is allocated
+ * stream-ordered (cudaMallocAsync) and released before return.  Errors: as
+ * for genie_make_queries and genie_search; INVALID_ARG for NULL buffers or
+ * h_q_off[0] != 0.
+ */
+genie_status genie_search_host(const genie_index* index, const uint32_t* h_q_off,
+                               const uint32_t* h_q_kw, uint32_t n_queries, uint32_t k,
+                               const uint32_t* h_k, const genie_search_opts* opts, uint32_t* h_ids,
+                               uint32_t* h_counts, uint32_t* h_n_valid, genie_stream stream);
+
+/*
  * Fills *out with the shape genie_search(index, queries, k, ..., opts, ...)
  * would launch (opts may be NULL).  Host only: no device work, no
  * synchronisation.  Automatic choices: counters wide enough for the largest
@@ -286,20 +310,66 @@ genie_status genie_search_shape(const genie_index* index, const genie_queries* q
                                 const genie_search_opts* opts, genie_search_shape_info* out);
 
 /* ------------------------------------------------------------------------ */
+/* GEN-SPQ ablation: Count Table + bucket k-selection (Sec. 6.1.2, App. A)    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  uint32_t buckets;    /* buckets per k-selection iteration, 2..32 (0 = 16) */
+  uint32_t reserved;   /* 0 */
+  uint64_t max_bytes;  /* device memory for Count Tables and candidate lists
+                          (0 = 8 GiB); queries run in passes that fit it */
+} genie_spq_opts;
+
+typedef struct {
+  uint64_t count_table_bytes_per_query;  /* 4 B per object: the dense counts */
+  uint64_t list_bytes_per_query;         /* 8 B per object: explicit (count, id) keys */
+  uint32_t queries_per_pass;
+  uint32_t passes;
+  double mean_iterations;                /* bucket-selection iterations per query */
+} genie_spq_info;
+
+/*
+ * The paper's GEN-SPQ: the same index and compiled queries, counted into a
+ * dense Count Table in device memory (a 32-bit count per object per query,
+ * Sec. 3.3's Count Table, one block per query keyword with global atomic
+ * adds, Sec. 3.2), then the top-k of each query's row by the bucket
+ * k-selection of Appendix A: each iteration buckets the candidates by
+ * floor((count - min) / (max - min) * buckets), keeps the buckets above the
+ * one that holds the k-th largest, and repeats on that bucket; all-equal
+ * candidates are taken in ascending id.  An ablation of c-PQ: results equal
+ * genie_search's (count desc, id asc); it uses 12 bytes per object per query
+ * of device memory instead of c-PQ's on-chip counters.
+ *   k, d_k, d_ids, d_counts, d_n_valid: as for genie_search.
+ *   opts: NULL for defaults.  info: NULL, or receives memory per query,
+ *   queries per pass and the mean iterations (then the call synchronises).
+ * Scratch is allocated stream-ordered and released before return.  Reads the
+ * query offsets back (synchronises `stream` once).  Errors: INVALID_ARG,
+ * CAPACITY (one query exceeds max_bytes), OUT_OF_MEMORY, CUDA.
+ */
+genie_status genie_search_spq(const genie_index* index, const genie_queries* queries, uint32_t k,
+                              const uint32_t* d_k, const genie_spq_opts* opts, uint32_t* d_ids,
+                              uint32_t* d_counts, uint32_t* d_n_valid, genie_spq_info* info,
+                              genie_stream stream);
+
+/* ------------------------------------------------------------------------ */
 /* Device calibration                                                        */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-  double smem_atomics_per_s;  /* shared-memory atomic adds with return per second, whole GPU */
+  double smem_atomics_per_s;      /* integer adds of a 16-bit lane's increment to its 32-bit
+                                     word, old word returned and used; per second, whole GPU */
   uint32_t sms;
-  double seconds;             /* duration of the timed launch */
+  double seconds;                 /* duration of the timed launch of the first form */
+  double smem_red_per_s;          /* the same adds with no value returned (red) */
+  double smem_f16_atomics_per_s;  /* binary16 adds of 1.0 to a 16-bit lane, old value returned */
+  double smem_f16_red_per_s;      /* binary16 adds of 1.0 with no value returned */
 } genie_calibration;
 
 /*
- * Measure the ceiling of the scan kernel's counter updates: one block per SM
- * fills a 128 KB shared counter array and every thread issues atomic adds of
- * 16-bit lane increments at pseudo-random words, using each returned value.
- * Synchronises the device.  The paper has no counterpart.
+ * Measure the ceilings of the scan kernel's counter updates: one block per SM
+ * fills a 128 KB shared counter array and every thread adds to 16-bit lanes
+ * at pseudo-random positions, in the four forms above.  Synchronises the
+ * device.  The paper has no counterpart.
  */
 genie_status genie_calibrate(genie_calibration* out);
 
@@ -370,18 +440,23 @@ genie_status genie_batch_run(genie_batch* batch, const genie_queries* queries, c
  * to `streams` batches in flight on their own CUDA streams; whenever one
  * finishes, the queued requests that fit are admitted into the next batch,
  * so requests arriving while others run overlap with them on the device.
- * Admission is by counter memory: each in-flight query holds n_objects x
- * bits / 8 bytes of the budget (the Bitmap Counter of Sec. 3.3.1) until its
- * batch completes.  Results equal genie_search's for the same query.  Device
- * memory is allocated once at creation; the loop itself neither allocates
- * nor synchronises per batch.
+ * Admission is by device memory: each in-flight request holds, until its
+ * batch completes, the bytes it occupies in its launch slot's buffers --
+ * request_bytes_base (its per-query words, its result rows, its rows of
+ * per-range candidate lists and count histogram) plus 4 bytes per keyword.
+ * The Bitmap Counters themselves (Sec. 3.3.1) live in shared memory of the
+ * blocks that count them; their n_objects x W / 8 bytes per query are
+ * reported (bc_bytes_in_flight), not charged.  Results equal genie_search's
+ * for the same query.  Device memory is allocated once at creation (streams
+ * x slot_bytes); the loop itself neither allocates nor synchronises per
+ * batch.
  */
 typedef struct genie_server genie_server;
 
 typedef struct {
-  uint64_t bc_budget_bytes;    /* counter bytes of all in-flight queries (default 8 GiB) */
-  uint32_t bits_per_object;    /* counter bits charged per object per query (0 = the
-                                  query's counter width: 4, 8 or 16) */
+  uint64_t mem_budget_bytes;   /* device bytes all in-flight requests may hold (0 = the
+                                  slots' total, streams x slot_bytes) */
+  uint32_t reserved;           /* 0 */
   uint32_t max_batch;          /* queries per launch (default 256) */
   uint32_t max_query_keywords; /* keywords per request (default 4096) */
   uint32_t k_max;              /* largest k of a request (default 100) */
@@ -400,10 +475,14 @@ typedef struct {
 typedef struct {
   uint64_t launches;               /* batches launched */
   uint64_t queries;                /* queries launched */
-  uint64_t deferred_admissions;    /* requests that waited for counter budget */
+  uint64_t deferred_admissions;    /* requests that waited for the memory budget */
   uint64_t max_queries_in_flight;  /* largest number of queries on the device at once */
   uint64_t pending;                /* queued now */
-  uint64_t reserved_bytes;         /* counter budget held now */
+  uint64_t reserved_bytes;         /* device bytes held by in-flight requests now */
+  uint64_t slot_bytes;             /* device memory of one launch slot */
+  uint64_t request_bytes_base;     /* slot bytes of one request besides its keywords */
+  uint64_t mem_budget_bytes;       /* the budget in force */
+  uint64_t bc_bytes_in_flight;     /* Bitmap-Counter bytes of the in-flight queries */
 } genie_server_stats;
 
 /* Monotonic clock of the server, in seconds. */
@@ -514,7 +593,9 @@ genie_status genie_mlp_seeds(genie_mlp* mlp, const genie_queries* queries, float
  *     genie_search); opts is otherwise honoured.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, once per device, with that device current).
- *     Make that first call before any stream capture on that device.
+ *     Make that first call before any stream capture on that device.  The
+ *     address is kept for the life of the process: after cudaDeviceReset on
+ *     a device, this entry point must not be used on that device again.
  *   - Every call uses the same array.  Calls whose work overlaps on the GPU
  *     (different streams, or different host threads) race on it; serialise
  *     them, e.g. by issuing them on one stream.
@@ -590,6 +671,25 @@ genie_status genie_parts_search(genie_parts* parts, const uint32_t* d_q_off, con
                                 uint32_t n_queries, uint32_t k, const uint32_t* d_k,
                                 uint32_t* d_ids, uint32_t* d_counts, uint32_t* d_n_valid,
                                 genie_stream stream);
+
+/*
+ * Exact merge of per-part top-k lists on the host: the result merge of the
+ * multiple-loading method (Sec. 3.4, Table 4), and the exchange step of a
+ * search whose objects are sharded over several GPUs (each searches its
+ * shard; the lists meet on one host).  No device work.
+ *   h_ids[p], h_counts[p] [n_queries * k_part] uint32, HOST: part p's
+ *              results with GLOBAL object ids, as genie_search writes them
+ *              (ranked by count desc, id asc; padding id 0xFFFFFFFF, count 0).
+ *   k          1 .. GENIE_MAX_K result slots per query of the output.
+ *   h_ids_out, h_counts_out [n_queries * k], h_n_valid [n_queries]: HOST.
+ * The output is the top-k of the union of the lists under (count desc, id
+ * asc): the top-k over all parts' objects when every part kept its top-k
+ * (k_part >= k) and no object is in two parts.  Errors: INVALID_ARG.
+ */
+genie_status genie_merge_host(uint32_t n_parts, const uint32_t* const* h_ids,
+                              const uint32_t* const* h_counts, uint32_t n_queries, uint32_t k_part,
+                              uint32_t k, uint32_t* h_ids_out, uint32_t* h_counts_out,
+                              uint32_t* h_n_valid);
 
 /* ------------------------------------------------------------------------ */
 /* Sequence search by ordered n-grams (Sec. 5.1, the shotgun-and-assembly    */

@@ -115,6 +115,19 @@ __device__ __forceinline__ uint32_t atom_add_shared(uint32_t saddr, uint32_t v) 
   return old;
 }
 
+// Shared-memory adds with no value returned (red), for counting without the
+// Gate; the second only where slot < len (unsigned).
+__device__ __forceinline__ void red_add_shared(uint32_t saddr, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(saddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_shared_in(uint32_t slot, uint32_t len, uint32_t saddr,
+                                                  uint32_t v) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.lt.u32 q, %0, %1;\n\t@q red.shared.add.u32 [%2], %3;\n\t}"
+      ::"r"(slot), "r"(len), "r"(saddr), "r"(v)
+      : "memory");
+}
+
 // The same, done only where slot < len (unsigned; the address is not touched
 // otherwise); returns 0 where it is not done.
 __device__ __forceinline__ uint32_t atom_add_shared_in(uint32_t slot, uint32_t len, uint32_t saddr,
@@ -171,18 +184,80 @@ __device__ uint32_t collect_lanes(const uint32_t* bc, uint32_t nwords, uint32_t 
   return min(found, limit);
 }
 
-// Number of lanes whose count is at least `value` (all threads of the block).
+// Largest count of the range (all threads of the block call it).
 template <int LOG2W>
-__device__ uint32_t count_at_least(const uint32_t* bc, uint32_t nwords, uint32_t value,
-                                   uint32_t* scratch) {
+__device__ uint32_t max_count(const uint32_t* bc, uint32_t nwords, uint32_t* scratch) {
   constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, MASK = (1u << W) - 1u;
   uint32_t m = 0;
   for (uint32_t w = threadIdx.x; w < nwords; w += blockDim.x) {
     const uint32_t word = bc[w];
+    if (word) {
 #pragma unroll
-    for (uint32_t l = 0; l < PER; ++l) m += ((word >> (l * W)) & MASK) >= value;
+      for (uint32_t l = 0; l < PER; ++l) m = max(m, (word >> (l * W)) & MASK);
+    }
   }
-  return dev::block_sum(m, scratch);
+  m = __reduce_max_sync(0xFFFFFFFFu, m);
+  __syncthreads();  // scratch may still be read by a previous call
+  if (dev::lane_id() == 0) scratch[dev::warp_id()] = m;
+  __syncthreads();
+  if (dev::warp_id() == 0) {
+    uint32_t v = dev::lane_id() < (blockDim.x >> 5) ? scratch[dev::lane_id()] : 0u;
+    v = __reduce_max_sync(0xFFFFFFFFu, v);
+    if (dev::lane_id() == 0) scratch[32] = v;
+  }
+  __syncthreads();
+  return scratch[32];
+}
+
+// How many counters of the range are at least x1, x2 and x3, in one pass
+// over the words (all threads of the block call it).
+template <int LOG2W>
+__device__ void count_at_least3(const uint32_t* bc, uint32_t nwords, uint32_t x1, uint32_t x2,
+                                uint32_t x3, unsigned long long* scratch, uint32_t out[3]) {
+  constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, MASK = (1u << W) - 1u;
+  uint32_t m1 = 0, m2 = 0, m3 = 0;
+  for (uint32_t w = threadIdx.x; w < nwords; w += blockDim.x) {
+    const uint32_t word = bc[w];
+    if (word) {
+#pragma unroll
+      for (uint32_t l = 0; l < PER; ++l) {
+        const uint32_t v = (word >> (l * W)) & MASK;
+        m1 += v >= x1;
+        m2 += v >= x2;
+        m3 += v >= x3;
+      }
+    }
+  }
+  // at most 2^18 counters per range: three 21-bit fields
+  const unsigned long long s = dev::block_sum<unsigned long long>(
+      m1 | ((unsigned long long)m2 << 21) | ((unsigned long long)m3 << 42), scratch);
+  out[0] = (uint32_t)(s & 0x1FFFFFu);
+  out[1] = (uint32_t)((s >> 21) & 0x1FFFFFu);
+  out[2] = (uint32_t)(s >> 42);
+}
+
+// The k-th largest count t of the range (0 when fewer than k counters are
+// >= 1): the largest x with #{count >= x} >= k.  One pass for the maximum M,
+// then a four-way search of [1, M] with three thresholds counted per pass
+// (a binary search of [1, B] would take log2 B passes).  All threads call it.
+template <int LOG2W>
+__device__ uint32_t kth_count(const uint32_t* bc, uint32_t nwords, uint32_t k, uint32_t* scratch,
+                              unsigned long long* scratch64) {
+  const uint32_t M = max_count<LOG2W>(bc, nwords, scratch);
+  uint32_t lo = 0, hi = M;  // #{>= lo} >= k (or lo = 0) and #{>= hi + 1} < k
+  while (lo < hi) {
+    const uint32_t span = hi - lo;  // candidates lo + 1 .. hi
+    const uint32_t y1 = lo + (span + 3) / 4;
+    const uint32_t y2 = max(y1, lo + (span + 1) / 2);
+    const uint32_t y3 = max(y2, lo + (3 * span + 3) / 4);
+    uint32_t c[3];
+    count_at_least3<LOG2W>(bc, nwords, y1, y2, y3, scratch64, c);
+    if (c[2] >= k) lo = y3;
+    else if (c[1] >= k) { lo = y2; hi = y3 - 1; }
+    else if (c[0] >= k) { lo = y1; hi = y2 - 1; }
+    else hi = y1 - 1;
+  }
+  return lo;
 }
 
 template <int LOG2W>
@@ -397,6 +472,7 @@ struct BlockShared {
   uint32_t next_run;  // next run of tiles to be claimed
   GateCtx gate;       // the Gate's pointers and query constants
   uint32_t scratch[33];
+  unsigned long long scratch64[33];
 };
 
 // One (query, object range) work item: reset the range's c-PQ in shared
@@ -551,7 +627,18 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
       // lines 1-2); val = the counter word before the add (0 for slots
       // outside the list).  Every id of a sublist lies in this block's range.
       uint32_t val[4 * kUnroll];
-      if (start >= lo && start + kTile <= hi) {
+      if (gateless) {  // counting only: no old value is needed
+        const uint32_t d0 = start + lane * 4 - lo, len = hi - lo;
+        const bool inside = start >= lo && start + kTile <= hi;
+#pragma unroll
+        for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
+          const uint32_t u = i >> 2, e = i & 3;
+          const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
+          const uint32_t saddr = bc_adj + Lane<LOG2W>::byte_off(id);
+          if (inside) red_add_shared(saddr, Lane<LOG2W>::inc(id));
+          else red_add_shared_in(d0 + u * 128 + e, len, saddr, Lane<LOG2W>::inc(id));
+        }
+      } else if (start >= lo && start + kTile <= hi) {
 #pragma unroll
         for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
           const uint32_t u = i >> 2, e = i & 3;
@@ -623,14 +710,9 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   const uint32_t nwords_local = (n_local + PER - 1) / PER;
   if (gateless) {
     // the k-th count of the range: largest x with #{count >= x} >= k
-    uint32_t lo_x = 0, hi_x = B;
-    while (lo_x < hi_x) {
-      const uint32_t mid = (lo_x + hi_x + 1) >> 1;
-      if (count_at_least<LOG2W>(bc, nwords_local, mid, scratch) >= kq) lo_x = mid;
-      else hi_x = mid - 1;
-    }
+    const uint32_t t = kth_count<LOG2W>(bc, nwords_local, kq, scratch, S.scratch64);
     if (tid == 0) {
-      s_at = lo_x + 1;
+      s_at = t + 1;
       s_n = 0;
     }
   } else if (tid == 0) {

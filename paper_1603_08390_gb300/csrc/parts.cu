@@ -312,3 +312,60 @@ extern "C" genie_status genie_parts_search(genie_parts* ps, const uint32_t* d_q_
   if (e != cudaSuccess) return fail_cuda(e, "genie_parts_search");
   return GENIE_OK;
 }
+
+// ---------------------------------------------------------------------------
+// genie_merge_host: the result merge of the multiple-loading method on the host
+// ---------------------------------------------------------------------------
+//
+// Sec. 3.4 merges the per-part top-k lists on the CPU (Table 4, "Result
+// merge").  Every list is ranked by (count desc, id asc) and holds its part's
+// exact top-k, ties at its k-th count taken in ascending id; an object a part
+// left out is outranked by k objects of that part, so the union of the lists
+// holds the whole batch's top-k, and a k-way merge of the lists under the same
+// order yields it.  This is the exchange of an object-sharded search over
+// several GPUs: each GPU searches its shard, the lists meet on one host.
+
+extern "C" genie_status genie_merge_host(uint32_t n_parts, const uint32_t* const* h_ids,
+                                         const uint32_t* const* h_counts, uint32_t n_queries,
+                                         uint32_t k_part, uint32_t k, uint32_t* h_ids_out,
+                                         uint32_t* h_counts_out, uint32_t* h_n_valid) {
+  if (n_parts == 0 || !h_ids || !h_counts || !h_ids_out || !h_counts_out || !h_n_valid)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_merge_host: NULL argument or no part");
+  if (k == 0 || k > GENIE_MAX_K || k_part == 0 || k_part > GENIE_MAX_K)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_merge_host: k and k_part must be in 1..GENIE_MAX_K");
+  for (uint32_t p = 0; p < n_parts; ++p)
+    if (!h_ids[p] || !h_counts[p]) return fail(GENIE_ERR_INVALID_ARG, "genie_merge_host: NULL list");
+  std::vector<uint32_t> cur(n_parts);
+  for (uint64_t q = 0; q < n_queries; ++q) {
+    std::fill(cur.begin(), cur.end(), 0u);
+    uint32_t n = 0;
+    uint32_t* out_i = h_ids_out + q * k;
+    uint32_t* out_c = h_counts_out + q * k;
+    while (n < k) {
+      // the head of the list whose next entry ranks first: count desc, id asc
+      int best = -1;
+      uint32_t bc = 0, bi = 0;
+      for (uint32_t p = 0; p < n_parts; ++p) {
+        if (cur[p] >= k_part) continue;
+        const uint32_t c = h_counts[p][q * k_part + cur[p]], id = h_ids[p][q * k_part + cur[p]];
+        if (c == 0) continue;  // padding: the list has ended
+        if (best < 0 || c > bc || (c == bc && id < bi)) {
+          best = (int)p;
+          bc = c;
+          bi = id;
+        }
+      }
+      if (best < 0) break;
+      out_i[n] = bi;
+      out_c[n] = bc;
+      ++cur[best];
+      ++n;
+    }
+    h_n_valid[q] = n;
+    for (uint32_t j = n; j < k; ++j) {
+      out_i[j] = 0xFFFFFFFFu;
+      out_c[j] = 0;
+    }
+  }
+  return GENIE_OK;
+}

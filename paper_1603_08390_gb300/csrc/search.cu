@@ -309,6 +309,62 @@ extern "C" genie_status genie_search(const genie_index* index, const genie_queri
 }
 
 // ---------------------------------------------------------------------------
+// genie_search_host: queries in, results out, both in host memory
+// ---------------------------------------------------------------------------
+//
+// The stages of the paper's Table 2 that one batch goes through at query time
+// -- query transfer, match, select and the copy of the results back -- in one
+// call: the keyword CSR is copied to the device on the caller's stream,
+// compiled, searched, and the top-k lists are copied back; the call returns
+// once they are in the caller's host buffers.
+
+extern "C" genie_status genie_search_host(const genie_index* index, const uint32_t* h_q_off,
+                                          const uint32_t* h_q_kw, uint32_t n_queries, uint32_t k,
+                                          const uint32_t* h_k, const genie_search_opts* opts,
+                                          uint32_t* h_ids, uint32_t* h_counts,
+                                          uint32_t* h_n_valid, genie_stream stream) {
+  if (!index || !h_q_off || !h_ids || !h_counts || !h_n_valid)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search_host: NULL argument");
+  if (n_queries == 0 || n_queries > (1u << 24))
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search_host: n_queries must be in 1..2^24");
+  if (k == 0 || k > GENIE_MAX_K)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_search_host: k must be in 1..GENIE_MAX_K");
+  if (h_q_off[0] != 0) return fail(GENIE_ERR_INVALID_ARG, "genie_search_host: h_q_off[0] must be 0");
+  const uint64_t n_kw = h_q_off[n_queries];
+  if (n_kw && !h_q_kw) return fail(GENIE_ERR_INVALID_ARG, "genie_search_host: h_q_kw is NULL");
+  cudaStream_t s = as_stream(stream);
+  // one stream-ordered block: q_off | q_kw | k | ids | counts | n_valid
+  const uint64_t w_off = 0, w_kw = w_off + n_queries + 1, w_k = w_kw + n_kw;
+  const uint64_t w_ids = w_k + (h_k ? n_queries : 0), w_cnt = w_ids + (uint64_t)n_queries * k;
+  const uint64_t w_nv = w_cnt + (uint64_t)n_queries * k, words = w_nv + n_queries;
+  uint32_t* d = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&d, words * 4, s);
+  if (e != cudaSuccess) return fail(GENIE_ERR_OUT_OF_MEMORY, "genie_search_host: cudaMallocAsync failed");
+  genie_queries* qs = nullptr;
+  genie_status st = GENIE_OK;
+  e = cudaMemcpyAsync(d + w_off, h_q_off, (n_queries + 1) * 4ull, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && n_kw) e = cudaMemcpyAsync(d + w_kw, h_q_kw, n_kw * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && h_k) e = cudaMemcpyAsync(d + w_k, h_k, n_queries * 4ull, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) st = fail_cuda(e, "genie_search_host: copy of the queries");
+  if (st == GENIE_OK) st = genie_make_queries(index, d + w_off, d + w_kw, n_queries, stream, &qs);
+  if (st == GENIE_OK)
+    st = genie_search(index, qs, k, h_k ? d + w_k : nullptr, opts, d + w_ids, d + w_cnt, d + w_nv,
+                      stream);
+  if (st == GENIE_OK) {
+    const uint64_t res = (uint64_t)n_queries * k * 4;
+    e = cudaMemcpyAsync(h_ids, d + w_ids, res, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_counts, d + w_cnt, res, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_n_valid, d + w_nv, n_queries * 4ull, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) st = fail_cuda(e, "genie_search_host: copy of the results");
+  }
+  genie_queries_destroy(qs);
+  cudaFreeAsync(d, s);
+  e = cudaStreamSynchronize(s);
+  if (st == GENIE_OK && e != cudaSuccess) st = fail_cuda(e, "genie_search_host");
+  return st;
+}
+
+// ---------------------------------------------------------------------------
 // genie_search_noalloc: the same search with its scratch in a fixed device array
 // ---------------------------------------------------------------------------
 //

@@ -2,12 +2,14 @@
 //
 // Requests (host keyword sets with their k) enter a FIFO queue.  A worker
 // thread keeps up to `streams` launches in flight: whenever a launch slot is
-// free it admits queued requests into a new batch while the Bitmap-Counter
-// bytes of all in-flight queries (n_objects x counter bits / 8 per query, the
-// memory Sec. 3.3 charges a query; the counters themselves live in shared
-// memory here) stay within the budget, copies the batch to the device and
-// enqueues the scan + c-PQ + merge kernels on the slot's stream, followed by
-// the copy of the results back.  Requests that arrive while other batches run
+// free it admits queued requests into a new batch while the device memory of
+// all in-flight requests stays within the budget, copies the batch to the
+// device and enqueues the scan + c-PQ + merge kernels on the slot's stream,
+// followed by the copy of the results back.  A request is charged the slot
+// memory it occupies: its keywords, its per-query words, its result rows,
+// its rows of per-range candidate lists and of the count histogram.  (The
+// Bitmap Counters, the memory Sec. 3.3 charges a query, live in shared
+// memory of the blocks that count them and are only reported.)  Requests that arrive while other batches run
 // join the next slot that frees, so batches overlap on the device.  Nothing is
 // allocated and nothing blocks per batch: completion is observed with
 // cudaEventQuery.  The paper has no serving component.
@@ -36,7 +38,8 @@ struct Request {
   uint32_t k = 0;
   uint32_t bound = 0;
   uint64_t tag = 0;
-  uint64_t bc_bytes = 0;
+  uint64_t dev_bytes = 0;  // device memory it holds while in flight
+  uint64_t bc_bytes = 0;   // Bitmap-Counter bytes (reported only)
   double t_submit = 0.0;
   bool deferred = false;
 };
@@ -61,7 +64,8 @@ struct Slot {
   uint32_t *h_q_off = nullptr, *h_q_kw = nullptr, *h_bound = nullptr, *h_karr = nullptr;
   uint32_t *h_ids = nullptr, *h_counts = nullptr, *h_n_valid = nullptr;
   std::vector<Request> reqs;
-  uint64_t reserved = 0;
+  uint64_t reserved = 0;     // device bytes held by the requests of the batch
+  uint64_t bc_reserved = 0;  // their Bitmap-Counter bytes
   bool busy = false;
 };
 
@@ -78,7 +82,10 @@ struct genie_server {
   std::condition_variable cv_work, cv_done;
   std::deque<genie::Request> pending;
   std::deque<genie::Done> finished;
-  uint64_t reserved = 0;
+  uint64_t reserved = 0;        // device bytes held by in-flight requests
+  uint64_t bc_reserved = 0;     // their Bitmap-Counter bytes
+  uint64_t slot_bytes = 0;      // device memory of one launch slot
+  uint64_t per_query_bytes = 0; // slot memory of one request besides its keywords
   std::atomic<bool> stop{false};
   std::atomic<int> error{0};
   std::thread worker;
@@ -168,7 +175,9 @@ void worker_loop(genie_server* sv) {
         sv->finished.push_back(std::move(d));
       }
       sv->reserved -= s.reserved;
+      sv->bc_reserved -= s.bc_reserved;
       s.reserved = 0;
+      s.bc_reserved = 0;
       s.reqs.clear();
       s.busy = false;
       progressed = true;
@@ -182,15 +191,17 @@ void worker_loop(genie_server* sv) {
         uint64_t kw = 0;
         while (!sv->pending.empty() && s.reqs.size() < sv->opts.max_batch) {
           Request& r = sv->pending.front();
-          if (sv->reserved + r.bc_bytes > sv->opts.bc_budget_bytes) {
+          if (sv->reserved + r.dev_bytes > sv->opts.mem_budget_bytes) {
             if (!r.deferred) ++sv->n_deferred;  // waits for in-flight queries to finish
             r.deferred = true;
             break;
           }
           if (kw + r.kw.size() > kw_cap) break;
           kw += r.kw.size();
-          sv->reserved += r.bc_bytes;
-          s.reserved += r.bc_bytes;
+          sv->reserved += r.dev_bytes;
+          s.reserved += r.dev_bytes;
+          sv->bc_reserved += r.bc_bytes;
+          s.bc_reserved += r.bc_bytes;
           s.reqs.push_back(std::move(r));
           sv->pending.pop_front();
         }
@@ -249,7 +260,6 @@ extern "C" genie_status genie_server_create(const genie_index* index, const geni
   if (o.k_max == 0) o.k_max = 100;
   if (o.streams == 0) o.streams = 2;
   if (o.queue_capacity == 0) o.queue_capacity = 1u << 16;
-  if (o.bc_budget_bytes == 0) o.bc_budget_bytes = (uint64_t)8 << 30;
   if (o.k_max > GENIE_MAX_K || o.streams > 8 || o.max_batch > 65536 || o.max_query_keywords > 65535)
     return fail(GENIE_ERR_INVALID_ARG, "genie_server_create: options out of range");
   genie_server* sv = new (std::nothrow) genie_server();
@@ -289,6 +299,9 @@ extern "C" genie_status genie_server_create(const genie_index* index, const geni
       s.hint_hist_words = hist_words;
     }
     s.cand_bytes = cand;
+    sv->slot_bytes = (uint64_t)(o.max_batch + 1) * 4 + (uint64_t)kw_cap * 4 + 3ull * o.max_batch * 4 +
+                     2ull * o.max_batch * o.k_max * 4 + o.max_batch * 4ull + cand +
+                     s.hint_hist_words * 4;
     if (e == cudaSuccess) e = cudaMallocHost(&s.h_q_off, (o.max_batch + 1) * 4);
     if (e == cudaSuccess) e = cudaMallocHost(&s.h_q_kw, kw_cap * 4);
     if (e == cudaSuccess) e = cudaMallocHost(&s.h_bound, o.max_batch * 4);
@@ -303,6 +316,11 @@ extern "C" genie_status genie_server_create(const genie_index* index, const geni
     return e != cudaSuccess ? fail_cuda(e, "genie_server_create")
                             : fail(GENIE_ERR_INVALID_ARG, "genie_server_create: cannot plan the search");
   }
+  // a request's share of a slot: its keywords, then one row of everything
+  // else the slot holds per query
+  const uint64_t hist_row = sv->slots.empty() ? 0 : sv->slots[0].hint_hist_words / o.max_batch;
+  sv->per_query_bytes = 20 + 8ull * o.k_max + cand / o.max_batch + hist_row * 4;
+  if (sv->opts.mem_budget_bytes == 0) sv->opts.mem_budget_bytes = sv->slot_bytes * o.streams;
   sv->worker = std::thread(worker_loop, sv);
   *out = sv;
   return GENIE_OK;
@@ -337,11 +355,12 @@ extern "C" genie_status genie_server_submit(genie_server* sv, const uint32_t* h_
   r.bound = (uint32_t)std::min<uint64_t>(n_kw, cap);
   if (r.bound > GENIE_MAX_BOUND)
     return fail(GENIE_ERR_INVALID_ARG, "genie_server_submit: count bound exceeds GENIE_MAX_BOUND");
+  // the counter width the search picks for this bound (reported, Sec. 3.3.1)
   const uint32_t width = r.bound <= 15 ? 4 : (r.bound <= 255 ? 8 : 16);
-  const uint32_t bits = sv->opts.bits_per_object ? sv->opts.bits_per_object : width;
-  r.bc_bytes = ((uint64_t)sv->index->n_objects * bits + 7) / 8;
-  if (r.bc_bytes > sv->opts.bc_budget_bytes)
-    return fail(GENIE_ERR_CAPACITY, "genie_server_submit: one query's counters exceed the budget");
+  r.bc_bytes = ((uint64_t)sv->index->n_objects * width + 7) / 8;
+  r.dev_bytes = sv->per_query_bytes + 4ull * n_kw;
+  if (r.dev_bytes > sv->opts.mem_budget_bytes)
+    return fail(GENIE_ERR_CAPACITY, "genie_server_submit: one request needs more device memory than the budget");
   r.k = k;
   r.tag = tag;
   r.t_submit = now_s();
@@ -393,6 +412,10 @@ extern "C" genie_status genie_server_get_stats(genie_server* sv, genie_server_st
   out->max_queries_in_flight = sv->max_in_flight;
   out->pending = sv->pending.size();
   out->reserved_bytes = sv->reserved;
+  out->slot_bytes = sv->slot_bytes;
+  out->request_bytes_base = sv->per_query_bytes;
+  out->mem_budget_bytes = sv->opts.mem_budget_bytes;
+  out->bc_bytes_in_flight = sv->bc_reserved;
   return GENIE_OK;
 }
 

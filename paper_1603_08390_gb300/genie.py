@@ -38,6 +38,7 @@ EXPORTED = (
     "genie_batch_create", "genie_batch_get_info", "genie_batch_destroy", "genie_batch_run",
     "genie_server_clock", "genie_server_create", "genie_server_destroy", "genie_server_submit",
     "genie_server_poll", "genie_server_get_stats", "genie_server_replay", "genie_calibrate",
+    "genie_search_host", "genie_search_spq", "genie_merge_host",
     "genie_parts_create", "genie_parts_destroy", "genie_parts_add", "genie_parts_get_info",
     "genie_parts_search", "genie_sa_grams", "genie_sa_verify", "genie_lsh_pstable",
     "genie_lsh_rbh",
@@ -76,7 +77,7 @@ class BatchOpts(ctypes.Structure):
 
 
 class ServerOpts(ctypes.Structure):
-    _fields_ = [("bc_budget_bytes", ctypes.c_uint64), ("bits_per_object", ctypes.c_uint32),
+    _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("reserved", ctypes.c_uint32),
                 ("max_batch", ctypes.c_uint32), ("max_query_keywords", ctypes.c_uint32),
                 ("k_max", ctypes.c_uint32), ("streams", ctypes.c_uint32),
                 ("queue_capacity", ctypes.c_uint32)]
@@ -91,12 +92,27 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("queries", ctypes.c_uint64),
                 ("deferred_admissions", ctypes.c_uint64),
                 ("max_queries_in_flight", ctypes.c_uint64), ("pending", ctypes.c_uint64),
-                ("reserved_bytes", ctypes.c_uint64)]
+                ("reserved_bytes", ctypes.c_uint64), ("slot_bytes", ctypes.c_uint64),
+                ("request_bytes_base", ctypes.c_uint64), ("mem_budget_bytes", ctypes.c_uint64),
+                ("bc_bytes_in_flight", ctypes.c_uint64)]
 
 
 class Calibration(ctypes.Structure):
     _fields_ = [("smem_atomics_per_s", ctypes.c_double), ("sms", ctypes.c_uint32),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("smem_red_per_s", ctypes.c_double),
+                ("smem_f16_atomics_per_s", ctypes.c_double),
+                ("smem_f16_red_per_s", ctypes.c_double)]
+
+
+class SpqOpts(ctypes.Structure):
+    _fields_ = [("buckets", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("max_bytes", ctypes.c_uint64)]
+
+
+class SpqInfo(ctypes.Structure):
+    _fields_ = [("count_table_bytes_per_query", ctypes.c_uint64),
+                ("list_bytes_per_query", ctypes.c_uint64), ("queries_per_pass", ctypes.c_uint32),
+                ("passes", ctypes.c_uint32), ("mean_iterations", ctypes.c_double)]
 
 
 class SearchOpts(ctypes.Structure):
@@ -162,6 +178,14 @@ def load(path: Optional[str] = None):
         lib.genie_search.restype = st
         lib.genie_search_noalloc.argtypes = lib.genie_search.argtypes
         lib.genie_search_noalloc.restype = st
+        lib.genie_search_host.argtypes = [vp, vp, vp, u32, u32, vp, ctypes.POINTER(SearchOpts),
+                                          vp, vp, vp, vp]
+        lib.genie_search_host.restype = st
+        lib.genie_search_spq.argtypes = [vp, vp, u32, vp, ctypes.POINTER(SpqOpts), vp, vp, vp,
+                                         ctypes.POINTER(SpqInfo), vp]
+        lib.genie_search_spq.restype = st
+        lib.genie_merge_host.argtypes = [u32, vp, vp, u32, u32, u32, vp, vp, vp]
+        lib.genie_merge_host.restype = st
         lib.genie_search_shape.argtypes = [vp, vp, u32, ctypes.POINTER(SearchOpts),
                                            ctypes.POINTER(SearchShape)]
         lib.genie_search_shape.restype = st
@@ -374,6 +398,49 @@ def genie_search(index: Index, queries: Queries, k: int, d_ids, d_counts, d_n_va
     _check(lib.genie_search(index.handle, queries.handle, k, _ptr(d_k),
                             ctypes.byref(opts) if opts is not None else None, _ptr(d_ids),
                             _ptr(d_counts), _ptr(d_n_valid), _stream(stream)), lib)
+
+
+def genie_search_host(index: Index, h_q_off, h_q_kw, n_queries: int, k: int, h_ids, h_counts,
+                      h_n_valid, h_k=None, opts: Optional[SearchOpts] = None, stream=None) -> None:
+    """Queries and results in host memory: copy in, compile, search, copy back
+    (one C call; returns when the results are in the host buffers).  Host
+    buffers are CPU tensors (pinned for full copy speed) or raw addresses."""
+    lib = load()
+    _check(lib.genie_search_host(index.handle, _ptr(h_q_off), _ptr(h_q_kw), n_queries, k,
+                                 _ptr(h_k), ctypes.byref(opts) if opts is not None else None,
+                                 _ptr(h_ids), _ptr(h_counts), _ptr(h_n_valid), _stream(stream)),
+           lib)
+
+
+def genie_search_spq(index: Index, queries: Queries, k: int, d_ids, d_counts, d_n_valid, d_k=None,
+                     buckets: int = 0, max_bytes: int = 0, stream=None) -> SpqInfo:
+    """The GEN-SPQ ablation: dense Count Table + bucket k-selection (same results)."""
+    lib = load()
+    info = SpqInfo()
+    opts = SpqOpts(buckets=buckets, max_bytes=max_bytes)
+    _check(lib.genie_search_spq(index.handle, queries.handle, k, _ptr(d_k), ctypes.byref(opts),
+                                _ptr(d_ids), _ptr(d_counts), _ptr(d_n_valid), ctypes.byref(info),
+                                _stream(stream)), lib)
+    return info
+
+
+def genie_merge_host(ids_parts, counts_parts, k: int):
+    """Exact host merge of per-part result lists (numpy uint32 [Q, k_part]
+    each, global ids) into the top-k (ids, counts, n_valid)."""
+    import numpy as np
+    lib = load()
+    P = len(ids_parts)
+    ids_parts = [np.ascontiguousarray(a, dtype=np.uint32) for a in ids_parts]
+    counts_parts = [np.ascontiguousarray(a, dtype=np.uint32) for a in counts_parts]
+    Q, kp = ids_parts[0].shape
+    pi = (ctypes.c_void_p * P)(*[a.ctypes.data for a in ids_parts])
+    pc = (ctypes.c_void_p * P)(*[a.ctypes.data for a in counts_parts])
+    ids = np.empty((Q, k), dtype=np.uint32)
+    cnt = np.empty((Q, k), dtype=np.uint32)
+    nv = np.empty(Q, dtype=np.uint32)
+    _check(lib.genie_merge_host(P, pi, pc, Q, kp, k, ids.ctypes.data, cnt.ctypes.data,
+                                nv.ctypes.data), lib)
+    return ids, cnt, nv
 
 
 def genie_search_shape(index: Index, queries: Queries, k: int,

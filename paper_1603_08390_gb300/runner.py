@@ -174,3 +174,26 @@ def query_facts(queries: genie.Queries) -> dict:
     genie.genie_queries_export(queries, bound, entries, feats)
     return {"bound": u32(bound), "entries": entries.cpu().numpy().view(np.uint64),
             "features": feats.cpu().numpy().reshape(n, genie.N_FEATURES)}
+
+
+def shard_range(n_objects: int, rank: int, world: int):
+    """Object ids [lo, hi) of shard `rank` of `world` (contiguous, balanced)."""
+    return n_objects * rank // world, n_objects * (rank + 1) // world
+
+
+def gather_merge(ids: np.ndarray, counts: np.ndarray, k: int, dst: int = 0):
+    """The exchange of an object-sharded search over the ranks of the default
+    torch.distributed group: every rank gives its shard's results (uint32
+    [Q, k_part], global ids), they are gathered on rank `dst` and merged
+    exactly there by genie_merge_host.  Returns (ids, counts, n_valid) on
+    `dst`, None elsewhere."""
+    import torch.distributed as dist
+    world, rank = dist.get_world_size(), dist.get_rank()
+    q, kp = ids.shape
+    mine = torch.from_numpy(np.stack([ids, counts]).astype(np.uint32).view(np.int32).copy())
+    parts = [torch.empty_like(mine) for _ in range(world)] if rank == dst else None
+    dist.gather(mine, gather_list=parts, dst=dst)
+    if rank != dst:
+        return None
+    arrs = [p.numpy().view(np.uint32) for p in parts]
+    return genie.genie_merge_host([a[0] for a in arrs], [a[1] for a in arrs], k)

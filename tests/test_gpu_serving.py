@@ -1,6 +1,7 @@
 """The continuous-batching serving loop (GPU): every result is the same alone
 and in a mix of overlapping requests, equal to genie_search and the oracle;
-the counter budget bounds the queries in flight; bad requests are statuses."""
+the device-memory budget bounds the requests in flight, each charged the slot
+memory it occupies; bad requests are statuses."""
 import numpy as np
 import pytest
 import torch
@@ -35,11 +36,18 @@ def _row(ids, cnt, n):
 
 def test_each_result_is_the_same_alone_and_in_the_mix(served):
     w, idx = served
-    n_obj = w.n_objects
-    # budget for 8 queries of 8-bit counters in flight: a quarter of one slot's batch, so the
-    # burst below must be held back however fast the device serves it
-    opts = genie.ServerOpts(bc_budget_bytes=8 * n_obj, bits_per_object=8, max_batch=32,
-                            k_max=100, streams=3)
+    # a request is charged exactly its share of a launch slot's device buffers:
+    # the per-query rows (request_bytes_base) for each of max_batch requests,
+    # 4 bytes per keyword of the slot's keyword buffer, and the offsets' end word
+    probe = genie.Server(idx, genie.ServerOpts(max_batch=32, k_max=100, streams=3))
+    st0 = probe.stats()
+    probe.close()
+    assert st0.slot_bytes == 32 * st0.request_bytes_base + 4 * 32 * 4096 + 4
+    assert st0.mem_budget_bytes == 3 * st0.slot_bytes  # default: every slot's memory
+    # a budget of a quarter of one slot, so the burst below must be held back
+    # however fast the device serves it
+    budget = st0.slot_bytes // 4
+    opts = genie.ServerOpts(mem_budget_bytes=budget, max_batch=32, k_max=100, streams=3)
     srv = genie.Server(idx, opts)
     q_off = w.q_off.astype(np.int64)
     # alone: one request at a time
@@ -58,8 +66,10 @@ def test_each_result_is_the_same_alone_and_in_the_mix(served):
     arrival = np.cumsum(rng.exponential(1.0 / 5e6, w.n_queries))
     lat, ids, cnt, nv = srv.replay(w.q_off, w.q_kw, w.k, arrival)
     st = srv.stats()
-    assert st.max_queries_in_flight <= 8
+    min_request = st0.request_bytes_base + 4 * int(np.diff(w.q_off.astype(np.int64)).min())
+    assert st.max_queries_in_flight <= budget // min_request
     assert st.deferred_admissions > 0       # the budget held requests back
+    assert st.reserved_bytes == 0 and st.bc_bytes_in_flight == 0  # all returned
     assert st.launches < 2 * w.n_queries    # requests were batched together
     assert np.all(lat > 0)
     for i in range(w.n_queries):
@@ -80,10 +90,9 @@ def test_each_result_is_the_same_alone_and_in_the_mix(served):
 
 def test_bad_requests_are_statuses(served):
     w, idx = served
-    srv = genie.Server(idx, genie.ServerOpts(bc_budget_bytes=w.n_objects // 2, bits_per_object=8,
-                                             k_max=10))
+    srv = genie.Server(idx, genie.ServerOpts(mem_budget_bytes=1000, k_max=10))
     with pytest.raises(genie.GenieError) as e:
-        srv.submit(np.array([1, 2, 3]), 5, 0)      # one query's counters exceed the budget
+        srv.submit(np.array([1, 2, 3]), 5, 0)      # one request's memory exceeds the budget
     assert e.value.status == genie.GENIE_ERR_CAPACITY
     srv.close()
     srv = genie.Server(idx, genie.ServerOpts(k_max=10))
