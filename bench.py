@@ -52,7 +52,7 @@ WORKLOAD = ("lsh-4m: 4,000,000 objects x 256 p-stable LSH keywords (bucket width
 REF_SAMPLE = 16   # oracle queries per reference step
 CPU_SAMPLE = 96   # oracle queries for the cpu_baseline object
 LEGS = ("lsh1m", "sets4m-batched", "lsh4m-learned", "serving", "lsh4m-parts", "relational",
-        "seq1m")
+        "seq1m", "gen-spq")
 
 
 def parse(argv=None):
@@ -320,7 +320,18 @@ def cpq_stats(genie, idx, d_q_off, d_q_kw, Q, k, out, stream, entries, opts_kw=N
     st = stats.cpu().numpy()
     return {"gate_passes_per_posting": float(st[0]) / max(1, entries), "gate_passes": int(st[0]),
             "ht_inserts": int(st[1]), "blocks": int(st[4]), "blocks_bitmap_fallback": int(st[2]),
-            "blocks_gateless_unseeded": int(st[6]), "reruns": int(st[3]), "bad_ids": int(st[5])}
+            "blocks_gateless_unseeded": int(st[6]), "reruns": int(st[3]), "bad_ids": int(st[5]),
+            "dense_bitmaps_added": int(st[7])}
+
+
+def dense_info(idx, qs) -> dict:
+    """The index's dense keywords (object bitmaps) and the batch's share."""
+    from paper_1603_08390_gb300 import genie
+    qi = genie.QueriesInfo()
+    genie.load().genie_queries_get_info(qs.handle, genie.ctypes.byref(qi))
+    return {"keywords": int(idx.info.dense_keywords), "min_df": int(idx.info.dense_min_df),
+            "bytes": int(idx.info.dense_bytes),
+            "batch_postings_share": float(qi.n_dense_entries) / max(1, qi.n_entries)}
 
 
 def run_headline(args, rank, world, local, keep=None):
@@ -351,6 +362,7 @@ def run_headline(args, rank, world, local, keep=None):
     torch.cuda.synchronize()
     entries = qs.n_entries
     kernel = genie.genie_search_shape(idx, qs, K).kernel_name()
+    dense = dense_info(idx, qs)
     del qs
     scan_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
@@ -436,6 +448,7 @@ def run_headline(args, rank, world, local, keep=None):
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
         "cpq": cpq,
+        "dense_keywords": dense,
         "parity_sampled": {"queries": [int(r) for r in rows], "ok": bool(parity)},
         "index_build_s": build_s,
     }
@@ -893,7 +906,55 @@ def leg_seq(args):
             "gpu_launches": 7 * steps}
 
 
-LEG_FUNCS = {"lsh1m": leg_lsh1m, "sets4m-batched": leg_batched, "serving": leg_serving,
+def leg_spq(args):
+    """The GEN-SPQ ablation (Sec. 6.1.2, Appendix A) on the 1M-object LSH
+    batch: a dense Count Table per query filled with global atomics, then the
+    bucket k-selection, against c-PQ -- time and device memory per query
+    (Table 5's comparison)."""
+    import torch
+    import synth
+    from paper_1603_08390_gb300 import genie, runner
+
+    k = 100
+    w = synth.config(2)
+    idx = runner.build_index(w)
+    Q = w.n_queries
+    d_q_off, d_q_kw = runner.to_dev(w.q_off), runner.to_dev(w.q_kw)
+    out_s, out_c = runner.Outputs(Q, k), runner.Outputs(Q, k)
+    stream = torch.cuda.current_stream()
+    qs = genie.genie_make_queries(idx, d_q_off, d_q_kw, Q, stream)
+    info = genie.genie_search_spq(idx, qs, k, out_s.ids, out_s.counts, out_s.n_valid)
+    shape = genie.genie_search_shape(idx, qs, k)
+    spq = lambda: genie.genie_search_spq(idx, qs, k, out_s.ids, out_s.counts, out_s.n_valid,
+                                         stream=stream, want_info=False)
+    cpq = lambda: genie.genie_search(idx, qs, k, out_c.ids, out_c.counts, out_c.n_valid,
+                                     stream=stream)
+    spq()
+    cpq()
+    steps = 3
+    s_ms, _ = timed_steps(spq, steps, stream)
+    c_ms, _ = timed_steps(cpq, steps, stream)
+    a, b = out_s.host(), out_c.host()
+    same = all(np.array_equal(a[x], b[x]) for x in a)
+    # c-PQ's device memory per query: its per-range candidate lists, the
+    # shared k-th count and count histogram, and its result rows (the
+    # counters themselves live in shared memory of the blocks)
+    cpq_bytes = shape.n_groups * k * 8 + 4 + (qs.max_bound + 2) * 4 + 2 * k * 4 + 4
+    spq_bytes = info.count_table_bytes_per_query + info.list_bytes_per_query + 2 * k * 4 + 4
+    return {"config": {"workload": "GEN-SPQ vs c-PQ on lsh-1m: 1,000,000 objects x 256 LSH "
+                                   "keywords, 1024 queries, k=100", "n_queries": Q, "k": k},
+            "value": Q * steps / (s_ms / 1e3), "ms_per_step": s_ms / steps,
+            "gen_spq": {"ms_per_step": s_ms / steps, "value": Q * steps / (s_ms / 1e3),
+                        "bytes_per_query": spq_bytes, "queries_per_pass": info.queries_per_pass,
+                        "passes": info.passes, "bucket_iterations_mean": info.mean_iterations},
+            "c_pq": {"ms_per_step": c_ms / steps, "value": Q * steps / (c_ms / 1e3),
+                     "bytes_per_query": cpq_bytes},
+            "c_pq_speedup": s_ms / c_ms, "memory_ratio": spq_bytes / cpq_bytes,
+            "identical_results": bool(same),
+            "parity_sampled": {"ok": parity_sampled(w, a, sampled_rows(Q))}}
+
+
+LEG_FUNCS = {"lsh1m": leg_lsh1m, "gen-spq": leg_spq, "sets4m-batched": leg_batched, "serving": leg_serving,
              "relational": leg_relational, "seq1m": leg_seq}
 
 
@@ -933,7 +994,7 @@ def run_genie(args, rank, world, local):
             keep.clear()
             gc.collect()
             torch.cuda.empty_cache()
-            for name in ("lsh1m", "sets4m-batched", "serving", "relational", "seq1m"):
+            for name in ("lsh1m", "gen-spq", "sets4m-batched", "serving", "relational", "seq1m"):
                 legs[name] = run_leg(name, args, keep)
             line["legs"] = legs
             line["suite_wall_s"] = time.perf_counter() - t0

@@ -77,7 +77,21 @@ typedef struct {
   uint32_t n_chunks;       /* ceil(n_objects / 2^chunk_shift) */
   uint32_t reserved;
   uint64_t device_bytes;   /* device memory held by the index */
+  uint32_t dense_keywords; /* keywords that also have an object bitmap */
+  uint32_t dense_min_df;   /* the list length from which a keyword has one */
+  uint64_t dense_bytes;    /* device memory of the bitmaps and their map */
 } genie_index_info;
+
+/* Build options (genie_build_index_ex). */
+typedef struct {
+  uint32_t chunk_shift;    /* as for genie_build_index (0 = default) */
+  uint32_t dense_min_df;   /* keywords whose list holds at least this many objects are also
+                              stored as object bitmaps (n_objects bits each), which the search
+                              adds whole instead of scanning the list: 0 = the default,
+                              max(64, ceil(n_objects / 32)), from which a bitmap is no larger
+                              than the list; GENIE_NO_DENSE = none */
+} genie_index_opts;
+#define GENIE_NO_DENSE 0xFFFFFFFFu
 
 /*
  * Build the inverted index on the device from objects given as keyword sets.
@@ -110,6 +124,19 @@ genie_status genie_build_index(const uint32_t* d_obj_off, const uint32_t* d_obj_
                                uint32_t n_objects, uint32_t vocab, uint32_t chunk_shift,
                                genie_stream stream, genie_index** out);
 
+/*
+ * genie_build_index with options.  Besides the List Array, keywords with
+ * dense lists (opts->dense_min_df) get an object bitmap: a search adds a
+ * dense keyword's bitmap to the query's counters with bitwise adders (32
+ * objects per operation) instead of one counter update per posting, then
+ * scans only the sparse keywords' lists.  The counts, and so every result,
+ * are those of the plain scan.  opts may be NULL (the defaults of
+ * genie_build_index).
+ */
+genie_status genie_build_index_ex(const uint32_t* d_obj_off, const uint32_t* d_obj_kw,
+                                  uint32_t n_objects, uint32_t vocab, const genie_index_opts* opts,
+                                  genie_stream stream, genie_index** out);
+
 /* Release an index (NULL is ignored).  Synchronises the device. */
 void genie_index_destroy(genie_index* index);
 
@@ -135,6 +162,7 @@ typedef struct {
   uint32_t max_bound;      /* largest count bound B_q over the batch */
   uint64_t n_keywords;     /* keywords after expansion, with multiplicity */
   uint64_t n_entries;      /* postings the batch scans: sum over queries of sum of df */
+  uint64_t n_dense_entries; /* of them, postings of keywords with an object bitmap */
 } genie_queries_info;
 
 /*
@@ -243,6 +271,13 @@ typedef struct {
  * of Sec. 6.1.2, with the counters on chip).  Same results. */
 #define GENIE_SEARCH_NO_GATE 2u
 
+/* Dense keywords (genie_build_index_ex) are added as object bitmaps, and
+ * their lists skipped, when they carry at least half the batch's postings;
+ * NO_DENSE scans every list, DENSE adds the bitmaps whatever their share.
+ * Same results either way. */
+#define GENIE_SEARCH_NO_DENSE 4u
+#define GENIE_SEARCH_DENSE 8u
+
 /*
  * Top-k of every query.  By default the ranges of a query share what they
  * learn: a range starts its AuditThreshold at the largest k-th count of the
@@ -271,6 +306,8 @@ typedef struct {
   uint32_t unroll;         /* 16-byte loads in flight per thread */
   uint32_t ht_slots;       /* hash-table slots per block */
   uint64_t smem_bytes;     /* dynamic shared memory per block */
+  uint32_t dense;          /* 1: dense keywords are added as object bitmaps */
+  uint32_t reserved;
 } genie_search_shape_info;
 
 /*

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(1024) order_kernel(const BatchDesc* __restrict
     D->order[i] = 0xFFFFFFu - (uint32_t)(keys[i] & 0xFFFFFFull);
 }
 
-template <int LOG2W, int U, int THREADS>
+template <int LOG2W, int U, int THREADS, bool DENSE>
 __global__ void __launch_bounds__(THREADS, 1) batch_cpq_kernel(const BatchDesc* __restrict__ D) {
   extern __shared__ uint4 smem_raw[];
   __shared__ BlockShared S;
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(THREADS, 1) batch_cpq_kernel(const BatchDesc* 
     if (item >= total) break;
     const uint32_t g = item / Q;
     const uint32_t qi = D->order[item - g * Q];
-    cpq_item<LOG2W, U>(SA, qi, g, smem_raw, S);
+    cpq_item<LOG2W, U, DENSE>(SA, qi, g, smem_raw, S);
     __threadfence();  // this item's candidate list, visible to the merging block
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(&D->done[qi], 1u) == G - 1;
@@ -106,8 +106,9 @@ __global__ void __launch_bounds__(THREADS, 1) batch_cpq_kernel(const BatchDesc* 
 // stream capture begins)
 template <int LOG2W, int U, int THREADS>
 cudaError_t launch_batch(const BatchDesc* d, uint32_t blocks, size_t smem, cudaStream_t s,
-                         bool launch) {
-  auto kern = batch_cpq_kernel<LOG2W, U, THREADS>;
+                         bool launch, bool dense) {
+  auto kern = (LOG2W >= 3 && dense) ? batch_cpq_kernel<LOG2W, U, THREADS, LOG2W >= 3>
+                                    : batch_cpq_kernel<LOG2W, U, THREADS, false>;
   if (!launch) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   kern<<<blocks, THREADS, smem, s>>>(d);
   return cudaGetLastError();
@@ -115,14 +116,14 @@ cudaError_t launch_batch(const BatchDesc* d, uint32_t blocks, size_t smem, cudaS
 
 template <int LOG2W>
 cudaError_t batch_width(const BatchDesc* d, uint32_t blocks, size_t smem, uint32_t threads,
-                        uint32_t unroll, cudaStream_t s, bool launch) {
-  if (threads == 512) return unroll == 8 ? launch_batch<LOG2W, 8, 512>(d, blocks, smem, s, launch)
-                                         : launch_batch<LOG2W, 4, 512>(d, blocks, smem, s, launch);
-  if (threads == 768) return unroll == 4 ? launch_batch<LOG2W, 4, 768>(d, blocks, smem, s, launch)
-                                         : launch_batch<LOG2W, 2, 768>(d, blocks, smem, s, launch);
-  if (threads == 896) return launch_batch<LOG2W, 2, 896>(d, blocks, smem, s, launch);
-  return unroll == 4 ? launch_batch<LOG2W, 4, 1024>(d, blocks, smem, s, launch)
-                     : launch_batch<LOG2W, 2, 1024>(d, blocks, smem, s, launch);
+                        uint32_t unroll, cudaStream_t s, bool launch, bool dense) {
+  if (threads == 512) return unroll == 8 ? launch_batch<LOG2W, 8, 512>(d, blocks, smem, s, launch, dense)
+                                         : launch_batch<LOG2W, 4, 512>(d, blocks, smem, s, launch, dense);
+  if (threads == 768) return unroll == 4 ? launch_batch<LOG2W, 4, 768>(d, blocks, smem, s, launch, dense)
+                                         : launch_batch<LOG2W, 2, 768>(d, blocks, smem, s, launch, dense);
+  if (threads == 896) return launch_batch<LOG2W, 2, 896>(d, blocks, smem, s, launch, dense);
+  return unroll == 4 ? launch_batch<LOG2W, 4, 1024>(d, blocks, smem, s, launch, dense)
+                     : launch_batch<LOG2W, 2, 1024>(d, blocks, smem, s, launch, dense);
 }
 
 cudaError_t batch_dispatch(const genie_batch* b, bool launch);
@@ -152,6 +153,8 @@ struct genie_batch {
   uint32_t max_queries = 0, max_bound = 0, k = 0;
   uint32_t log2w = 0, block_shift = 0, n_groups = 0, threads = 0, unroll = 0, ht_slots = 0;
   uint32_t blocks = 0;
+  bool dense = false;      // the instantiation being captured adds dense keywords' bitmaps
+  bool can_dense = false;  // the index has object bitmaps: a second graph adds them
   size_t smem = 0;
   genie::BatchDesc host_desc{};
   genie::BatchDesc* desc = nullptr;
@@ -160,8 +163,8 @@ struct genie_batch {
   uint32_t* counters = nullptr;  // [0] work, [1 ..] done, [max_queries] seeds, histograms
   uint64_t counter_words = 0;
   cudaStream_t capture_stream = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph[2] = {nullptr, nullptr};      // [1]: dense keywords as bitmaps
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
 };
 
 using namespace genie;
@@ -170,9 +173,9 @@ namespace genie {
 namespace {
 cudaError_t batch_dispatch(const genie_batch* b, bool launch) {
   cudaStream_t s = b->capture_stream;
-  return b->log2w == 2 ? batch_width<2>(b->desc, b->blocks, b->smem, b->threads, b->unroll, s, launch)
-       : b->log2w == 3 ? batch_width<3>(b->desc, b->blocks, b->smem, b->threads, b->unroll, s, launch)
-                       : batch_width<4>(b->desc, b->blocks, b->smem, b->threads, b->unroll, s, launch);
+  return b->log2w == 2 ? batch_width<2>(b->desc, b->blocks, b->smem, b->threads, b->unroll, s, launch, b->dense)
+       : b->log2w == 3 ? batch_width<3>(b->desc, b->blocks, b->smem, b->threads, b->unroll, s, launch, b->dense)
+                       : batch_width<4>(b->desc, b->blocks, b->smem, b->threads, b->unroll, s, launch, b->dense);
 }
 }  // namespace
 }  // namespace genie
@@ -180,8 +183,10 @@ cudaError_t batch_dispatch(const genie_batch* b, bool launch) {
 namespace {
 void free_batch(genie_batch* b) {
   if (!b) return;
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
+  for (int i = 0; i < 2; ++i) {
+    if (b->exec[i]) cudaGraphExecDestroy(b->exec[i]);
+    if (b->graph[i]) cudaGraphDestroy(b->graph[i]);
+  }
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   cudaFree(b->desc);
   cudaFree(b->cand);
@@ -228,6 +233,10 @@ extern "C" genie_status genie_batch_create(const genie_index* index, uint32_t ma
   b->unroll = p.unroll;
   b->ht_slots = p.ht_slots;
   b->smem = p.smem;
+  // a batch's queries are known only when it runs: with object bitmaps in the
+  // index, a second graph adds them, and each run picks one (as genie_search
+  // does, by the share of the batch's postings the dense keywords carry)
+  b->can_dense = index->n_dense && p.log2w >= 3;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
   b->blocks = (opts && opts->blocks) ? opts->blocks : (uint32_t)sms;
@@ -259,6 +268,9 @@ extern "C" genie_status genie_batch_create(const genie_index* index, uint32_t ma
   d.scan.k = k;
   d.scan.block_shift = p.block_shift;
   d.scan.chunks_per_block = 1u << (p.block_shift - index->chunk_shift);
+  d.scan.dense_slot = b->can_dense ? index->dense_slot : nullptr;
+  d.scan.dense_bits = b->can_dense ? index->dense_bits : nullptr;
+  d.scan.map_words = index->map_words;
   d.scan.n_groups = p.n_groups;
   d.scan.ht_slots = p.ht_slots;
   d.scan.za_len = p.za_len;
@@ -277,16 +289,19 @@ extern "C" genie_status genie_batch_create(const genie_index* index, uint32_t ma
   cudaStream_t cs = b->capture_stream;
   const size_t osmem = (size_t)dev::next_pow2(std::min(max_queries, kOrderCap)) * 8;
   e = cudaFuncSetAttribute(order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem);
-  if (e == cudaSuccess) e = batch_dispatch(b, false);
-  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    cudaMemsetAsync(b->counters, 0, b->counter_words * 4, cs);
-    order_kernel<<<1, 1024, osmem, cs>>>(b->desc);
-    cudaError_t le = batch_dispatch(b, true);
-    e = cudaStreamEndCapture(cs, &b->graph);
-    if (e == cudaSuccess && le != cudaSuccess) e = le;
+  for (int gi = 0; gi < (b->can_dense ? 2 : 1) && e == cudaSuccess; ++gi) {
+    b->dense = gi == 1;
+    e = batch_dispatch(b, false);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaMemsetAsync(b->counters, 0, b->counter_words * 4, cs);
+      order_kernel<<<1, 1024, osmem, cs>>>(b->desc);
+      cudaError_t le = batch_dispatch(b, true);
+      e = cudaStreamEndCapture(cs, &b->graph[gi]);
+      if (e == cudaSuccess && le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[gi], b->graph[gi], 0);
   }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
   if (e != cudaSuccess) {
     free_batch(b);
     return fail_cuda(e, "genie_batch_create: graph capture");
@@ -352,7 +367,9 @@ extern "C" genie_status genie_batch_run(genie_batch* b, const genie_queries* que
   d.entries = queries->entries;
   // pageable source: the runtime stages it before returning, so `d` may go
   GENIE_CUDA_TRY(cudaMemcpyAsync(b->desc, &d, sizeof(d), cudaMemcpyHostToDevice, s));
-  GENIE_CUDA_TRY(cudaGraphLaunch(b->exec, s));
+  const bool dense = b->can_dense && queries->n_dense_entries > 0 &&
+                     2 * queries->n_dense_entries >= queries->n_entries;
+  GENIE_CUDA_TRY(cudaGraphLaunch(b->exec[dense ? 1 : 0], s));
   return GENIE_OK;
 }
 

@@ -53,6 +53,11 @@ struct ScanArgs {
   // 1: count only, then select from the Bitmap Counter (the Gate and the
   // hash table stay idle) -- the GEN-SPQ-style ablation of Sec. 6.1.2
   uint32_t no_gate;
+  // dense keywords (NULL: none): dense_slot[kw] = the keyword's object bitmap
+  // or kNoDense; bitmap s = dense_bits[s * map_words ..]
+  const uint32_t* dense_slot;
+  const uint32_t* dense_bits;
+  uint64_t map_words;
 };
 
 constexpr uint32_t kMaxProbe = 32;   // hash-table probes before an insert gives up
@@ -266,6 +271,131 @@ __device__ __forceinline__ uint32_t lane_count(const uint32_t* bc, uint32_t loca
   return (vld(&bc[local >> LPW]) >> ((local & (PER - 1)) << LOG2W)) & MASK;
 }
 
+// ---------------------------------------------------------------------------
+// Dense keywords: their object bitmaps are added whole
+// ---------------------------------------------------------------------------
+//
+// A keyword whose list holds a large share of the objects is also stored as
+// an object bitmap.  A block adds the bitmaps of its query's dense keywords to
+// the Bitmap Counter before it scans the sparse keywords' lists: each thread
+// sums its 32-object bitmap words over the keywords in bit-sliced counters
+// (slice j holds bit j of 32 counts; full adders on whole words, three
+// inputs per two bitwise operations), then turns the slices into counts with
+// an 8 x 8 bit transpose and adds them to the counter words it owns.  The
+// counts are those the lists would give, one per (keyword, object) pair.
+
+// Full adder on 32 bit positions at once: l = a ^ b ^ c (weight 1), h =
+// majority(a, b, c) (weight 2).
+__device__ __forceinline__ void csa(uint32_t& h, uint32_t& l, uint32_t a, uint32_t b, uint32_t c) {
+  const uint32_t u = a ^ b;
+  h = (a & b) | (u & c);
+  l = u ^ c;
+}
+
+// s[0..7] (bit-sliced counts, weights 1, 2, ..., 128) += x.
+__device__ __forceinline__ void slices_add1(uint32_t (&s)[8], uint32_t x) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint32_t t = s[j] & x;
+    s[j] ^= x;
+    x = t;
+  }
+}
+
+// s += x[0] + ... + x[7]: a carry-save tree for the low three weights, the
+// weight-8 carry rippled into the rest.
+__device__ __forceinline__ void slices_add8(uint32_t (&s)[8], const uint32_t* x) {
+  uint32_t t2a, t2b, t4a, t4b, t8;
+  csa(t2a, s[0], s[0], x[0], x[1]);
+  csa(t2b, s[0], s[0], x[2], x[3]);
+  csa(t4a, s[1], s[1], t2a, t2b);
+  csa(t2a, s[0], s[0], x[4], x[5]);
+  csa(t2b, s[0], s[0], x[6], x[7]);
+  csa(t4b, s[1], s[1], t2a, t2b);
+  csa(t8, s[2], s[2], t4a, t4b);
+#pragma unroll
+  for (int j = 3; j < 8; ++j) {
+    const uint32_t t = s[j] & t8;
+    s[j] ^= t8;
+    t8 = t;
+  }
+}
+
+// Counts of objects 8q .. 8q+7 of a bitmap word from its slices, one byte
+// each (byte c = count of object 8q + c): the 8 x 8 bit matrix with row j =
+// byte q of slice j, transposed (three delta swaps).
+template <int Q>
+__device__ __forceinline__ unsigned long long slice_bytes(const uint32_t (&s)[8]) {
+  constexpr uint32_t sel = Q | ((Q + 4) << 4);
+  const uint32_t lo = __byte_perm(__byte_perm(s[0], s[1], sel), __byte_perm(s[2], s[3], sel), 0x5410);
+  const uint32_t hi = __byte_perm(__byte_perm(s[4], s[5], sel), __byte_perm(s[6], s[7], sel), 0x5410);
+  unsigned long long x = ((unsigned long long)hi << 32) | lo, t;
+  t = (x ^ (x >> 7)) & 0x00AA00AA00AA00AAull;
+  x ^= t ^ (t << 7);
+  t = (x ^ (x >> 14)) & 0x0000CCCC0000CCCCull;
+  x ^= t ^ (t << 14);
+  t = (x ^ (x >> 28)) & 0x00000000F0F0F0F0ull;
+  x ^= t ^ (t << 28);
+  return x;
+}
+
+// Adds the counts of bitmap word w (local objects 32w .. 32w+31) to the
+// counter words that hold them (8-bit lanes: four objects per word; 16-bit:
+// two).  The calling thread owns those counter words.
+template <int LOG2W>
+__device__ __forceinline__ void slices_emit(uint32_t* bc, uint32_t w, const uint32_t (&s)[8]) {
+  if (!(s[0] | s[1] | s[2] | s[3] | s[4] | s[5] | s[6] | s[7])) return;
+  const unsigned long long c[4] = {slice_bytes<0>(s), slice_bytes<1>(s), slice_bytes<2>(s),
+                                   slice_bytes<3>(s)};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t lo = (uint32_t)c[q], hi = (uint32_t)(c[q] >> 32);
+    if (LOG2W == 3) {
+      bc[8 * w + 2 * q] += lo;
+      bc[8 * w + 2 * q + 1] += hi;
+    } else {  // 16-bit lanes: objects 2i, 2i+1 in the low and high halves
+      bc[16 * w + 4 * q] += __byte_perm(lo, 0u, 0x4140);
+      bc[16 * w + 4 * q + 1] += __byte_perm(lo, 0u, 0x4342);
+      bc[16 * w + 4 * q + 2] += __byte_perm(hi, 0u, 0x4140);
+      bc[16 * w + 4 * q + 3] += __byte_perm(hi, 0u, 0x4342);
+    }
+  }
+}
+
+// What the dense phase needs of the search arguments (passed by value: a
+// reference to a kernel's parameters would copy them to local memory).
+struct DenseArgs {
+  const uint32_t* dense_slot;
+  const uint32_t* dense_bits;
+  const uint32_t* q_kw;
+  uint64_t map_words;
+  uint32_t block_shift;
+};
+
+// Adds the object bitmaps slots[0..n) (n <= 255) of range g to the Bitmap
+// Counter.  Each thread takes 32-object words in turn and reads sixteen
+// bitmaps' words at a time; all threads call it.
+template <int LOG2W>
+__device__ void dense_add(const DenseArgs& A, uint32_t g, uint32_t* bc, const uint32_t* slots,
+                          uint32_t n) {
+  const uint32_t nwr = (1u << A.block_shift) >> 5;  // bitmap words of the range
+  const uint32_t* __restrict__ bits = A.dense_bits + (uint64_t)g * nwr;
+  const uint64_t mw = A.map_words;
+  for (uint32_t w = threadIdx.x; w < nwr; w += blockDim.x) {
+    uint32_t s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t d = 0;
+    for (; d + 16 <= n; d += 16) {
+      uint32_t x[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) x[e] = __ldg(bits + slots[d + e] * mw + w);
+      slices_add8(s, x);
+      slices_add8(s, x + 8);
+    }
+    for (; d < n; ++d) slices_add1(s, __ldg(bits + slots[d] * mw + w));
+    slices_emit<LOG2W>(bc, w, s);
+  }
+}
+
 // State the Gate touches, all in shared memory of one block.
 struct GateState {
   uint32_t* za;       // ZipperArray, 1-based
@@ -470,18 +600,108 @@ struct BlockShared {
   uint32_t gateless;  // count only, then select from the Bitmap Counter
   uint32_t tie_floor; // ties below it are left out of the read-out
   uint32_t next_run;  // next run of tiles to be claimed
+  uint32_t n_dense;   // dense keywords whose bitmaps the range added
   GateCtx gate;       // the Gate's pointers and query constants
   uint32_t scratch[33];
   unsigned long long scratch64[33];
 };
+
+// The dense keywords of query keywords q_kw[qa..qb) for range g: their
+// bitmaps are added to the Bitmap Counter (the lists are not scanned).  Then,
+// for a range that runs the Gate (gated), the ZipperArray is set to what the
+// Gate would hold after these counts -- ZA[i] = #objects with count >= i for
+// i >= AT (each object passes every level up to its count) -- AT advances
+// past the full levels, and the objects at or above the new AT (fewer than
+// k) enter the hash table.  list: 2 * kKwBatch words of shared memory.
+// Returns the number of dense keywords added.  All threads call it.
+template <int LOG2W>
+__device__ __noinline__ uint32_t dense_phase(const DenseArgs A, uint32_t g, uint32_t qa, uint32_t qb,
+                                             uint32_t* bc, uint32_t nwords, uint32_t* list,
+                                             bool gated, BlockShared& S) {
+  constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, MASK = (1u << W) - 1u;
+  const uint32_t tid = threadIdx.x, cap = 2 * kKwBatch;
+  uint32_t total = 0;
+  for (uint32_t kb = qa; kb < qb; kb += cap) {
+    const uint32_t nk = min(cap, qb - kb);
+    if (tid == 0) S.n = 0;
+    __syncthreads();
+    for (uint32_t i = tid; i < nk; i += blockDim.x) {
+      const uint32_t sl = A.dense_slot[A.q_kw[kb + i]];
+      if (sl != kNoDense) list[atomicAdd(&S.n, 1u)] = sl;
+    }
+    __syncthreads();
+    const uint32_t nd = S.n;
+    for (uint32_t d0 = 0; d0 < nd; d0 += 255) dense_add<LOG2W>(A, g, bc, list + d0, min(255u, nd - d0));
+    total += nd;
+    __syncthreads();  // the list is refilled, the counters are read next
+  }
+  if (!gated || total == 0) return total;
+  GateCtx& G = S.gate;
+  uint32_t* za = G.g.za;
+  const uint32_t at0 = S.at, B = G.B;
+  // ZA[c] = #objects with count c (c >= at0) ...
+  for (uint32_t w = tid; w < nwords; w += blockDim.x) {
+    const uint32_t word = bc[w];
+    if (word) {
+#pragma unroll
+      for (uint32_t l = 0; l < PER; ++l) {
+        const uint32_t c = (word >> (l * W)) & MASK;
+        if (c >= at0 && c <= B) atomicAdd(&za[c], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  // ... then suffix sums over [at0, B] by warp 0, 32 levels per step from the top
+  if (tid < 32) {
+    uint32_t carry = 0;
+    for (int top = (int)B; top >= (int)at0; top -= 32) {
+      const int c = top - (int)tid;
+      uint32_t v = c >= (int)at0 ? za[c] : 0u;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, v, d);
+        if ((int)tid >= d) v += o;
+      }
+      if (c >= (int)at0) za[c] = v + carry;
+      carry += __shfl_sync(0xFFFFFFFFu, v, 31);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t a = at0;
+    while (a <= B && za[a] >= G.kq) ++a;
+    S.at = a;
+  }
+  __syncthreads();
+  const uint32_t a = S.at;
+  if (a <= B && za[a] > 0) {  // fewer than k objects: presence bits and hash-table entries
+    for (uint32_t w = tid; w < nwords; w += blockDim.x) {
+      const uint32_t word = bc[w];
+      if (word) {
+#pragma unroll
+        for (uint32_t l = 0; l < PER; ++l) {
+          if (((word >> (l * W)) & MASK) >= a) {
+            const uint32_t local = w * PER + l;
+            atomicOr(&G.g.present[local >> 5], 1u << (local & 31));
+            ht_insert<LOG2W>(G.g, G.obj_base + local, G.obj_base, G.ht_mask, G.ht_bits);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  return total;
+}
 
 // One (query, object range) work item: reset the range's c-PQ in shared
 // memory, scan the postings of the query's keywords inside the range through
 // the Bitmap Counter and the Gate, then write the range's exact top-k
 // (Theorem 3.1) as result keys to A.cand.  All threads of the block call it.
 // LOG2W: log2 of the counter width; U: 16-byte loads in flight per lane (a
-// warp tile is 128 * U postings).
-template <int LOG2W, int U>
+// warp tile is 128 * U postings); DENSE: the range adds the bitmaps of the
+// query's dense keywords and scans only the other lists (a separate
+// instantiation, so that the plain scan's code is untouched by the dense one).
+template <int LOG2W, int U, bool DENSE>
 __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_t g,
                                          uint4* smem_raw, BlockShared& S) {
   constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, LPW = 5 - LOG2W;
@@ -542,9 +762,20 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   const bool gateless = S.gateless;
   // every count of the range stays below the top bit of its lane
   const bool swar = S.gate.B < (1u << ((1u << LOG2W) - 1));
+  const uint32_t qa = A.q_off[q], qb = A.q_off[q + 1];
+  // dense keywords first: their bitmaps are added whole, their lists skipped
+  // (the count stays in shared memory: the scan loop has no register to spare)
+  if (DENSE && LOG2W >= 3) {
+    const uint32_t nd = dense_phase<LOG2W>(DenseArgs{A.dense_slot, A.dense_bits, A.q_kw,
+                                                     A.map_words, A.block_shift},
+                                           g, qa, qb, bc, nwords, reinterpret_cast<uint32_t*>(seg),
+                                           !gateless, S);
+    if (tid == 0) S.n_dense = nd;
+  } else if (tid == 0) {
+    S.n_dense = 0;
+  }
 
   // ---- scan: all postings of the query's keywords inside this id range ---
-  const uint32_t qa = A.q_off[q], qb = A.q_off[q + 1];
   const uint32_t stride = A.n_chunks + 1;
   // a register copy: A may live in shared memory (persistent blocks), which
   // the counter atomics' memory clobbers would make the loop reload
@@ -557,9 +788,13 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     uint32_t ntiles = 0;
     if (tid < nk) {
       const uint32_t kw = A.q_kw[kb + tid];
-      const uint64_t base = A.kw_off[kw];
-      const uint32_t* row = A.chunk_pos + (uint64_t)kw * stride;
-      const uint32_t lo = (uint32_t)(base + row[c0]), hi = (uint32_t)(base + row[c1]);
+      uint32_t lo = 0, hi = 0;
+      if (!DENSE || LOG2W < 3 || A.dense_slot[kw] == kNoDense) {  // a dense keyword's list is skipped
+        const uint64_t base = A.kw_off[kw];
+        const uint32_t* row = A.chunk_pos + (uint64_t)kw * stride;
+        lo = (uint32_t)(base + row[c0]);
+        hi = (uint32_t)(base + row[c1]);
+      }
       seg[tid] = make_uint2(lo, hi);
       ntiles = hi > lo ? (hi - (lo & ~3u) + kTile - 1) / kTile : 0;
     }
@@ -777,6 +1012,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     atomicAdd(&A.stats[1], (unsigned long long)S.gate.n_ins);
     if (!certified && !gateless) atomicAdd(&A.stats[2], 1ull);
     if (gateless) atomicAdd(&A.stats[6], 1ull);
+    if (S.n_dense) atomicAdd(&A.stats[7], (unsigned long long)S.n_dense);
     atomicAdd(&A.stats[4], 1ull);
     if (s_flags[1]) atomicAdd(&A.stats[5], 1ull);
   }
@@ -784,12 +1020,12 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
 
 // One block per (query, object range).  LOG2W: log2 of the counter width; U:
 // 16-byte loads in flight per lane (a warp tile is 128 * U postings);
-// THREADS: the block size.
-template <int LOG2W, int U, int THREADS>
+// THREADS: the block size; DENSE: dense keywords are added as bitmaps.
+template <int LOG2W, int U, int THREADS, bool DENSE>
 __global__ void __launch_bounds__(THREADS, 1) scan_cpq_kernel(const ScanArgs A) {
   extern __shared__ uint4 smem_raw[];
   __shared__ BlockShared S;
-  cpq_item<LOG2W, U>(A, blockIdx.x % A.n_sel, blockIdx.x / A.n_sel, smem_raw, S);
+  cpq_item<LOG2W, U, DENSE>(A, blockIdx.x % A.n_sel, blockIdx.x / A.n_sel, smem_raw, S);
 }
 
 // ---------------------------------------------------------------------------
@@ -931,6 +1167,7 @@ __global__ void check_k_kernel(uint32_t n_queries, uint32_t k, const uint32_t* _
 constexpr double kLongSublist = 4096.0;
 
 struct Plan {
+  bool dense;  // the scan adds dense keywords' bitmaps
   uint32_t log2w;
   uint32_t unroll;
   uint32_t block_shift;
@@ -974,6 +1211,11 @@ genie_status make_plan(const genie_index* idx, const genie_queries* qs, uint32_t
   if (p->threads == 512 ? (p->unroll != 4 && p->unroll != 8) : (p->unroll != 2 && p->unroll != 4))
     return fail(GENIE_ERR_INVALID_ARG, "genie_search: unroll must be 2 or 4 (768 or 1024 threads), 4 or 8 (512)");
   p->za_len = B + 2;
+  // Dense keywords' bitmaps pay when they carry most of the batch's postings
+  // (their instantiation of the scan is slower on the lists it still scans).
+  p->dense = idx->n_dense && p->log2w >= 3 && !(o && (o->flags & GENIE_SEARCH_NO_DENSE)) &&
+             ((o && (o->flags & GENIE_SEARCH_DENSE)) ||
+              (2 * qs->n_dense_entries >= qs->n_entries && qs->n_dense_entries > 0));
   p->smem = scan_smem_bytes(p->log2w, shift, slots, p->za_len, k);
   int dev = 0, max_smem = 0;
   cudaGetDevice(&dev);

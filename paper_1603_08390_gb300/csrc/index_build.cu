@@ -174,6 +174,31 @@ __global__ void sublist_map_kernel(const uint64_t* __restrict__ kw_off, const ui
   }
 }
 
+// Object bitmaps of the dense keywords: one block per dense keyword; each
+// thread folds a run of its (ascending) ids into one word at a time and sets
+// it with one atomicOr when the word changes.
+__global__ void dense_fill_kernel(const uint64_t* __restrict__ kw_off,
+                                  const uint32_t* __restrict__ ids,
+                                  const uint32_t* __restrict__ dense_kw, uint64_t map_words,
+                                  uint32_t* __restrict__ bits) {
+  const uint32_t kw = dense_kw[blockIdx.x];
+  uint32_t* map = bits + (uint64_t)blockIdx.x * map_words;
+  const uint64_t a = kw_off[kw], b = kw_off[kw + 1];
+  const uint64_t per = (b - a + blockDim.x - 1) / blockDim.x;
+  const uint64_t lo = a + per * threadIdx.x, hi = min(b, lo + per);
+  uint32_t word = 0xFFFFFFFFu, acc = 0;
+  for (uint64_t p = lo; p < hi; ++p) {
+    const uint32_t id = ids[p];
+    if ((id >> 5) != word) {
+      if (acc) atomicOr(&map[word], acc);
+      word = id >> 5;
+      acc = 0;
+    }
+    acc |= 1u << (id & 31);
+  }
+  if (acc) atomicOr(&map[word], acc);
+}
+
 int grid_for(uint64_t n, int threads, int cap = 152 * 32) {
   uint64_t g = (n + threads - 1) / threads;
   return (int)std::max<uint64_t>(1, std::min<uint64_t>(g, (uint64_t)cap));
@@ -189,10 +214,11 @@ struct DevBuf {
 
 using namespace genie;
 
-extern "C" genie_status genie_build_index(const uint32_t* d_obj_off, const uint32_t* d_obj_kw,
-                                          uint32_t n_objects, uint32_t vocab,
-                                          uint32_t chunk_shift, genie_stream stream,
-                                          genie_index** out) {
+extern "C" genie_status genie_build_index_ex(const uint32_t* d_obj_off, const uint32_t* d_obj_kw,
+                                             uint32_t n_objects, uint32_t vocab,
+                                             const genie_index_opts* opts, genie_stream stream,
+                                             genie_index** out) {
+  uint32_t chunk_shift = opts ? opts->chunk_shift : 0u;
   if (!out) return fail(GENIE_ERR_INVALID_ARG, "genie_build_index: out is NULL");
   if (!d_obj_off) return fail(GENIE_ERR_INVALID_ARG, "genie_build_index: d_obj_off is NULL");
   if (n_objects == 0 || n_objects > (1u << 31))
@@ -272,6 +298,8 @@ extern "C" genie_status genie_build_index(const uint32_t* d_obj_off, const uint3
   auto cleanup = [&](genie_status st) {
     cudaFree(idx->kw_off);
     cudaFree(idx->chunk_pos);
+    cudaFree(idx->dense_slot);
+    cudaFree(idx->dense_bits);
     delete idx;
     return st;
   };
@@ -297,8 +325,66 @@ extern "C" genie_status genie_build_index(const uint32_t* d_obj_off, const uint3
     return cleanup(fail_cuda(e, "genie_build_index kernels"));
   }
   idx->device_bytes = ((uint64_t)vocab + 1) * 8 + padded * 4 + tab_n * 4;
+
+  // Dense keywords: lists of at least dense_min_df postings also become
+  // object bitmaps (n_objects bits, padded so that a search block's slice of
+  // up to 2^18 objects, plus one word, stays inside).
+  uint32_t min_df = opts ? opts->dense_min_df : 0u;
+  // default: a bitmap (n_objects bits) no larger than the list (32 bits a posting)
+  if (min_df == 0) min_df = std::max<uint32_t>(64u, (n_objects + 31) / 32);
+  idx->dense_min_df = min_df;
+  if (min_df != GENIE_NO_DENSE && nnz > 0) {
+    std::vector<uint64_t> h_off((size_t)vocab + 1);
+    e = cudaMemcpyAsync(h_off.data(), idx->kw_off, h_off.size() * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      cudaFree(idx->post_ids);
+      return cleanup(fail_cuda(e, "genie_build_index: list offsets"));
+    }
+    std::vector<uint32_t> slot(vocab, kNoDense), dense_kw;
+    for (uint32_t v = 0; v < vocab; ++v)
+      if (h_off[v + 1] - h_off[v] >= min_df) {
+        slot[v] = (uint32_t)dense_kw.size();
+        dense_kw.push_back(v);
+        idx->dense_postings += h_off[v + 1] - h_off[v];
+      }
+    if (!dense_kw.empty()) {
+      const uint64_t words = ((uint64_t)n_objects + 31) / 32 + 2;
+      idx->map_words = (words + 8191) / 8192 * 8192;
+      idx->n_dense = (uint32_t)dense_kw.size();
+      uint32_t* d_kw = nullptr;
+      e = cudaMalloc(&idx->dense_slot, (uint64_t)vocab * 4);
+      if (e == cudaSuccess) e = cudaMalloc(&idx->dense_bits, idx->n_dense * idx->map_words * 4);
+      if (e == cudaSuccess) e = cudaMalloc(&d_kw, dense_kw.size() * 4);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(idx->dense_slot, slot.data(), (uint64_t)vocab * 4, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d_kw, dense_kw.data(), dense_kw.size() * 4, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(idx->dense_bits, 0, idx->n_dense * idx->map_words * 4, s);
+      if (e == cudaSuccess) {
+        dense_fill_kernel<<<idx->n_dense, 256, 0, s>>>(idx->kw_off, idx->post_ids, d_kw,
+                                                       idx->map_words, idx->dense_bits);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      cudaFree(d_kw);
+      if (e != cudaSuccess) {
+        cudaFree(idx->post_ids);
+        return cleanup(fail_cuda(e, "genie_build_index: dense bitmaps"));
+      }
+      idx->device_bytes += (uint64_t)vocab * 4 + idx->n_dense * idx->map_words * 4;
+    }
+  }
   *out = idx;
   return GENIE_OK;
+}
+
+extern "C" genie_status genie_build_index(const uint32_t* d_obj_off, const uint32_t* d_obj_kw,
+                                          uint32_t n_objects, uint32_t vocab,
+                                          uint32_t chunk_shift, genie_stream stream,
+                                          genie_index** out) {
+  genie_index_opts o;
+  o.chunk_shift = chunk_shift;
+  o.dense_min_df = 0;
+  return genie_build_index_ex(d_obj_off, d_obj_kw, n_objects, vocab, &o, stream, out);
 }
 
 extern "C" void genie_index_destroy(genie_index* index) {
@@ -307,6 +393,8 @@ extern "C" void genie_index_destroy(genie_index* index) {
   cudaFree(index->kw_off);
   cudaFree(index->post_ids);
   cudaFree(index->chunk_pos);
+  cudaFree(index->dense_slot);
+  cudaFree(index->dense_bits);
   delete index;
 }
 
@@ -320,6 +408,9 @@ extern "C" genie_status genie_index_get_info(const genie_index* index, genie_ind
   out->n_chunks = index->n_chunks;
   out->reserved = 0;
   out->device_bytes = index->device_bytes;
+  out->dense_keywords = index->n_dense;
+  out->dense_min_df = index->dense_min_df;
+  out->dense_bytes = index->n_dense ? (uint64_t)index->vocab * 4 + index->n_dense * index->map_words * 4 : 0;
   return GENIE_OK;
 }
 

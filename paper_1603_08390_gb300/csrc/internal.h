@@ -28,7 +28,8 @@ genie_status search_raw(const genie_index* idx, const uint32_t* q_off, const uin
                         const uint32_t* d_k, unsigned long long* cand, size_t cand_bytes,
                         uint32_t* at_hint, uint32_t* hint_hist, size_t hint_hist_words,
                         uint32_t* ids, uint32_t* counts, uint32_t* n_valid, cudaStream_t s,
-                        uint64_t n_entries = 0, uint64_t n_keywords = 0);
+                        uint64_t n_entries = 0, uint64_t n_keywords = 0,
+                        uint64_t n_dense_entries = 0);
 
 // Largest per-query count histograms (bytes) a search allocates to seed the
 // AuditThreshold of later object ranges; beyond it the seed is the largest
@@ -56,8 +57,21 @@ struct genie_index {
   uint64_t* kw_off = nullptr;    // [vocab + 1]: list of keyword v = post_ids[kw_off[v] .. kw_off[v+1])
   uint32_t* post_ids = nullptr;  // [nnz rounded up to 4, + 4]: ascending ids per list, zero padded
   uint32_t* chunk_pos = nullptr; // [vocab * (n_chunks + 1)]: first position of ids >= c << chunk_shift, relative to kw_off[v]
+  // Keywords with a dense list also as object bitmaps: dense_slot[v] = the
+  // bitmap of keyword v (kNoDense if it has none); bitmap s is
+  // dense_bits[s * map_words ..], bit o set iff object o holds the keyword.
+  uint32_t n_dense = 0;
+  uint32_t dense_min_df = 0;     // lists of at least this many postings have a bitmap
+  uint64_t map_words = 0;        // 32-bit words per bitmap (padded)
+  uint64_t dense_postings = 0;   // postings of the keywords with a bitmap
+  uint32_t* dense_slot = nullptr;  // [vocab] or NULL when n_dense = 0
+  uint32_t* dense_bits = nullptr;  // [n_dense * map_words]
   uint64_t device_bytes = 0;
 };
+
+namespace genie {
+constexpr uint32_t kNoDense = 0xFFFFFFFFu;
+}  // namespace genie
 
 // Compiled queries: every query is a list of keywords (relational items
 // already expanded), with its count bound, scan volume and features.
@@ -68,6 +82,7 @@ struct genie_queries {
   uint32_t max_bound = 0;
   uint64_t n_keywords = 0;
   uint64_t n_entries = 0;
+  uint64_t n_dense_entries = 0;  // of them, postings of keywords with an object bitmap
   uint32_t* q_off = nullptr;     // [n_queries + 1]
   uint32_t* q_kw = nullptr;      // [n_keywords]
   uint32_t* bound = nullptr;     // [n_queries]

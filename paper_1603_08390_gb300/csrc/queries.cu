@@ -15,7 +15,7 @@ constexpr uint32_t kSortCap = 2048;  // queries up to this length get an exact m
 
 enum QFlag {
   kBadOffsets = 0, kBadKeyword = 1, kBadDim = 2, kBadRange = 3, kMaxBound = 4,
-  kTotalLo = 6, kTotalHi = 7, kNumQFlags = 8
+  kTotalLo = 6, kTotalHi = 7, kDenseLo = 8, kDenseHi = 9, kNumQFlags = 10
 };
 
 // Per query: copy of the keywords is already in place; compute B_q, the sum of
@@ -24,7 +24,8 @@ enum QFlag {
 __global__ void __launch_bounds__(kCompileThreads)
 compile_kernel(const uint32_t* __restrict__ q_off, const uint32_t* __restrict__ q_kw,
                uint32_t n_queries, uint64_t n_kw, const uint64_t* __restrict__ kw_off,
-               uint32_t vocab, uint32_t max_obj_len, const uint32_t* __restrict__ items_off,
+               uint32_t vocab, uint32_t max_obj_len, uint32_t dense_min_df,
+               const uint32_t* __restrict__ items_off,
                uint32_t* __restrict__ bound, uint64_t* __restrict__ entries,
                float* __restrict__ features, uint32_t* flags) {
   __shared__ unsigned long long sorted[kSortCap];
@@ -46,7 +47,7 @@ compile_kernel(const uint32_t* __restrict__ q_off, const uint32_t* __restrict__ 
     for (uint32_t f = threadIdx.x; f < kFeatures; f += blockDim.x) hist[f] = 0;
     if (threadIdx.x == 0) { max_run = len ? 1u : 0u; bad_kw = 0; }
     __syncthreads();
-    unsigned long long df_sum = 0;
+    unsigned long long df_sum = 0, dense_sum = 0;
     for (uint32_t i = a + threadIdx.x; i < b; i += blockDim.x) {
       uint32_t kw = q_kw[i];
       uint32_t bin = 0;
@@ -55,11 +56,13 @@ compile_kernel(const uint32_t* __restrict__ q_off, const uint32_t* __restrict__ 
       } else {
         uint64_t df = kw_off[kw + 1] - kw_off[kw];
         df_sum += df;
+        if (df >= dense_min_df) dense_sum += df;
         bin = df == 0 ? 0u : min(kFeatures - 1, 64u - (uint32_t)__clzll((long long)df));
       }
       atomicAdd(&hist[bin], 1u);
     }
     df_sum = dev::block_sum(df_sum, scratch64);
+    dense_sum = dev::block_sum(dense_sum, scratch64);
     // largest multiplicity of a keyword (exact for short queries)
     uint32_t mult = len;
     if (len <= kSortCap) {
@@ -87,6 +90,7 @@ compile_kernel(const uint32_t* __restrict__ q_off, const uint32_t* __restrict__ 
       entries[q] = df_sum;
       atomicMax(&flags[kMaxBound], bq);
       atomicAdd((unsigned long long*)&flags[kTotalLo], df_sum);
+      if (dense_sum) atomicAdd((unsigned long long*)&flags[kDenseLo], dense_sum);
       if (bad_kw) atomicOr(&flags[kBadKeyword], 1u);
     }
     __syncthreads();
@@ -176,6 +180,7 @@ genie_status finish(genie_queries* q, const uint32_t* items_off, uint32_t* flags
   int grid = (int)std::min<uint32_t>(q->n_queries, 152u * 16u);
   compile_kernel<<<grid, kCompileThreads, 0, s>>>(q->q_off, q->q_kw, q->n_queries, q->n_keywords,
                                                   idx->kw_off, idx->vocab, idx->max_object_len,
+                                                  idx->n_dense ? idx->dense_min_df : 0xFFFFFFFFu,
                                                   items_off, q->bound, q->entries, q->features, flags);
   cudaError_t e = cudaGetLastError();
   uint32_t h[kNumQFlags];
@@ -188,6 +193,7 @@ genie_status finish(genie_queries* q, const uint32_t* items_off, uint32_t* flags
     return fail(GENIE_ERR_INVALID_ARG, std::string(who) + ": a query's count bound exceeds GENIE_MAX_BOUND (too many items)");
   q->max_bound = h[kMaxBound];
   q->n_entries = (uint64_t)h[kTotalLo] | ((uint64_t)h[kTotalHi] << 32);
+  q->n_dense_entries = (uint64_t)h[kDenseLo] | ((uint64_t)h[kDenseHi] << 32);
   return GENIE_OK;
 }
 
@@ -317,6 +323,7 @@ extern "C" genie_status genie_queries_get_info(const genie_queries* queries, gen
   out->max_bound = queries->max_bound;
   out->n_keywords = queries->n_keywords;
   out->n_entries = queries->n_entries;
+  out->n_dense_entries = queries->n_dense_entries;
   return GENIE_OK;
 }
 

@@ -76,7 +76,9 @@ __global__ void add_stat_kernel(unsigned long long* stat, uint32_t v) { *stat +=
 
 template <int LOG2W, int U, int THREADS>
 cudaError_t launch_scan(const ScanArgs& a, const Plan& p, cudaStream_t s) {
-  auto kern = scan_cpq_kernel<LOG2W, U, THREADS>;
+  // the dense instantiation exists for 8- and 16-bit counters
+  auto kern = (LOG2W >= 3 && p.dense) ? scan_cpq_kernel<LOG2W, U, THREADS, LOG2W >= 3>
+                                      : scan_cpq_kernel<LOG2W, U, THREADS, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
   if (e != cudaSuccess) return e;
   const uint64_t blocks = (uint64_t)a.n_sel * a.n_groups;
@@ -134,6 +136,9 @@ cudaError_t run_pass(const genie_index* idx, const genie_queries* qs, uint32_t k
   a.hint_hist = at_hint ? hint_hist : nullptr;
   a.hint_stride = p.za_len;
   a.no_gate = (o && (o->flags & GENIE_SEARCH_NO_GATE)) ? 1u : 0u;
+  a.dense_slot = p.dense ? idx->dense_slot : nullptr;
+  a.dense_bits = p.dense ? idx->dense_bits : nullptr;
+  a.map_words = idx->map_words;
   const bool timed = o && !sel && o->scan_event_begin && o->scan_event_end;
   if (timed) cudaEventRecord((cudaEvent_t)o->scan_event_begin, s);
   cudaError_t e = dispatch_scan(a, p, s);
@@ -181,13 +186,14 @@ genie_status search_raw(const genie_index* idx, const uint32_t* q_off, const uin
                         const uint32_t* d_k, unsigned long long* cand, size_t cand_bytes,
                         uint32_t* at_hint, uint32_t* hint_hist, size_t hint_hist_words,
                         uint32_t* ids, uint32_t* counts, uint32_t* n_valid, cudaStream_t s,
-                        uint64_t n_entries, uint64_t n_keywords) {
+                        uint64_t n_entries, uint64_t n_keywords, uint64_t n_dense_entries) {
   genie_queries view;
   view.index = idx;
   view.n_queries = n;
   view.max_bound = max_bound;
   view.n_entries = n_entries;  // postings and keywords of the batch (0 if unknown): they pick
-  view.n_keywords = n_keywords;  // the default launch shape
+  view.n_keywords = n_keywords;
+  view.n_dense_entries = n_dense_entries;  // the default launch shape
   view.q_off = const_cast<uint32_t*>(q_off);
   view.q_kw = const_cast<uint32_t*>(q_kw);
   view.bound = const_cast<uint32_t*>(bound);
@@ -229,6 +235,8 @@ extern "C" genie_status genie_search_shape(const genie_index* index, const genie
   out->unroll = p.unroll;
   out->ht_slots = p.ht_slots;
   out->smem_bytes = p.smem;
+  out->dense = p.dense ? 1u : 0u;
+  out->reserved = 0;
   return GENIE_OK;
 }
 

@@ -35,6 +35,7 @@ double now_s() {
 struct Request {
   std::vector<uint32_t> kw;
   uint64_t entries = 0;  // postings its keywords' lists hold
+  uint64_t dense_entries = 0;  // of them, postings of keywords with an object bitmap
   uint32_t k = 0;
   uint32_t bound = 0;
   uint64_t tag = 0;
@@ -123,10 +124,11 @@ void free_slot(Slot& s) {
 void launch_slot(genie_server* sv, Slot& s) {
   const uint32_t n = (uint32_t)s.reqs.size(), kmax = sv->opts.k_max;
   uint32_t pos = 0, max_bound = 1;
-  uint64_t entries = 0;
+  uint64_t entries = 0, dense_entries = 0;
   for (uint32_t i = 0; i < n; ++i) {
     const Request& r = s.reqs[i];
     entries += r.entries;
+    dense_entries += r.dense_entries;
     s.h_q_off[i] = pos;
     std::memcpy(s.h_q_kw + pos, r.kw.data(), r.kw.size() * 4);
     pos += (uint32_t)r.kw.size();
@@ -142,7 +144,7 @@ void launch_slot(genie_server* sv, Slot& s) {
   cudaMemcpyAsync(s.karr, s.h_karr, n * 4, cudaMemcpyHostToDevice, st);
   genie_status gs = search_raw(sv->index, s.q_off, s.q_kw, s.bound, n, max_bound, kmax, s.karr,
                                s.cand, s.cand_bytes, s.hint, s.hint_hist, s.hint_hist_words, s.ids,
-                               s.counts, s.n_valid, st, entries, pos);
+                               s.counts, s.n_valid, st, entries, pos, dense_entries);
   if (gs != GENIE_OK) sv->error = gs;
   cudaMemcpyAsync(s.h_ids, s.ids, (size_t)n * kmax * 4, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(s.h_counts, s.counts, (size_t)n * kmax * 4, cudaMemcpyDeviceToHost, st);
@@ -348,7 +350,11 @@ extern "C" genie_status genie_server_submit(genie_server* sv, const uint32_t* h_
   r.kw.assign(h_kw, h_kw + n_kw);
   for (uint32_t v : r.kw) {
     if (v >= sv->index->vocab) return fail(GENIE_ERR_INVALID_ARG, "genie_server_submit: keyword >= vocab");
-    if (!sv->kw_off.empty()) r.entries += sv->kw_off[v + 1] - sv->kw_off[v];
+    if (!sv->kw_off.empty()) {
+      const uint64_t df = sv->kw_off[v + 1] - sv->kw_off[v];
+      r.entries += df;
+      if (sv->index->n_dense && df >= sv->index->dense_min_df) r.dense_entries += df;
+    }
   }
   // count bound as in genie_make_queries
   const uint64_t cap = (uint64_t)sv->index->max_object_len * max_multiplicity(r.kw);

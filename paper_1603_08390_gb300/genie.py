@@ -26,6 +26,9 @@ GENIE_MAX_K = 1024
 GENIE_MAX_BOUND = 4095
 GENIE_SEARCH_PER_RANGE_AT = 1
 GENIE_SEARCH_NO_GATE = 2
+GENIE_SEARCH_NO_DENSE = 4
+GENIE_SEARCH_DENSE = 8
+GENIE_NO_DENSE = 0xFFFFFFFF
 N_FEATURES = 64
 
 EXPORTED = (
@@ -38,7 +41,7 @@ EXPORTED = (
     "genie_batch_create", "genie_batch_get_info", "genie_batch_destroy", "genie_batch_run",
     "genie_server_clock", "genie_server_create", "genie_server_destroy", "genie_server_submit",
     "genie_server_poll", "genie_server_get_stats", "genie_server_replay", "genie_calibrate",
-    "genie_search_host", "genie_search_spq", "genie_merge_host",
+    "genie_search_host", "genie_search_spq", "genie_merge_host", "genie_build_index_ex",
     "genie_parts_create", "genie_parts_destroy", "genie_parts_add", "genie_parts_get_info",
     "genie_parts_search", "genie_sa_grams", "genie_sa_verify", "genie_lsh_pstable",
     "genie_lsh_rbh",
@@ -61,12 +64,19 @@ class IndexInfo(ctypes.Structure):
     _fields_ = [("n_objects", ctypes.c_uint32), ("vocab", ctypes.c_uint32),
                 ("nnz", ctypes.c_uint64), ("max_object_len", ctypes.c_uint32),
                 ("chunk_shift", ctypes.c_uint32), ("n_chunks", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64)]
+                ("reserved", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64),
+                ("dense_keywords", ctypes.c_uint32), ("dense_min_df", ctypes.c_uint32),
+                ("dense_bytes", ctypes.c_uint64)]
+
+
+class IndexOpts(ctypes.Structure):
+    _fields_ = [("chunk_shift", ctypes.c_uint32), ("dense_min_df", ctypes.c_uint32)]
 
 
 class QueriesInfo(ctypes.Structure):
     _fields_ = [("n_queries", ctypes.c_uint32), ("max_bound", ctypes.c_uint32),
-                ("n_keywords", ctypes.c_uint64), ("n_entries", ctypes.c_uint64)]
+                ("n_keywords", ctypes.c_uint64), ("n_entries", ctypes.c_uint64),
+                ("n_dense_entries", ctypes.c_uint64)]
 
 
 class BatchOpts(ctypes.Structure):
@@ -129,12 +139,14 @@ class SearchShape(ctypes.Structure):
     _fields_ = [("counter_bits", ctypes.c_uint32), ("block_shift", ctypes.c_uint32),
                 ("n_groups", ctypes.c_uint32), ("threads", ctypes.c_uint32),
                 ("unroll", ctypes.c_uint32), ("ht_slots", ctypes.c_uint32),
-                ("smem_bytes", ctypes.c_uint64)]
+                ("smem_bytes", ctypes.c_uint64), ("dense", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
     def kernel_name(self) -> str:
         """Name of the scan kernel this shape launches, as profilers print it."""
         log2w = {4: 2, 8: 3, 16: 4}[self.counter_bits]
-        return "scan_cpq_kernel<%d, %d, %d>" % (log2w, self.unroll, self.threads)
+        return "scan_cpq_kernel<%d, %d, %d, %s>" % (log2w, self.unroll, self.threads,
+                                                   "true" if self.dense else "false")
 
 
 _LIB = None
@@ -158,6 +170,9 @@ def load(path: Optional[str] = None):
         lib.genie_version.restype = st
         lib.genie_build_index.argtypes = [vp, vp, u32, u32, u32, vp, ctypes.POINTER(vp)]
         lib.genie_build_index.restype = st
+        lib.genie_build_index_ex.argtypes = [vp, vp, u32, u32, ctypes.POINTER(IndexOpts), vp,
+                                             ctypes.POINTER(vp)]
+        lib.genie_build_index_ex.restype = st
         lib.genie_index_destroy.argtypes = [vp]
         lib.genie_index_destroy.restype = None
         lib.genie_index_get_info.argtypes = [vp, ctypes.POINTER(IndexInfo)]
@@ -332,11 +347,19 @@ class Queries:
 
 
 def genie_build_index(d_obj_off, d_obj_kw, n_objects: int, vocab: int, chunk_shift: int = 0,
-                      stream=None) -> Index:
+                      stream=None, dense_min_df: Optional[int] = None) -> Index:
+    """Build the index; dense_min_df: None = the library's default threshold
+    for object bitmaps, GENIE_NO_DENSE = none, else that list length."""
     lib = load()
     out = ctypes.c_void_p()
-    _check(lib.genie_build_index(_ptr(d_obj_off), _ptr(d_obj_kw), n_objects, vocab, chunk_shift,
-                                 _stream(stream), ctypes.byref(out)), lib)
+    if dense_min_df is None:
+        _check(lib.genie_build_index(_ptr(d_obj_off), _ptr(d_obj_kw), n_objects, vocab,
+                                     chunk_shift, _stream(stream), ctypes.byref(out)), lib)
+    else:
+        opts = IndexOpts(chunk_shift=chunk_shift, dense_min_df=dense_min_df)
+        _check(lib.genie_build_index_ex(_ptr(d_obj_off), _ptr(d_obj_kw), n_objects, vocab,
+                                        ctypes.byref(opts), _stream(stream), ctypes.byref(out)),
+               lib)
     return Index(out.value)
 
 
@@ -413,13 +436,16 @@ def genie_search_host(index: Index, h_q_off, h_q_kw, n_queries: int, k: int, h_i
 
 
 def genie_search_spq(index: Index, queries: Queries, k: int, d_ids, d_counts, d_n_valid, d_k=None,
-                     buckets: int = 0, max_bytes: int = 0, stream=None) -> SpqInfo:
-    """The GEN-SPQ ablation: dense Count Table + bucket k-selection (same results)."""
+                     buckets: int = 0, max_bytes: int = 0, stream=None,
+                     want_info: bool = True) -> Optional[SpqInfo]:
+    """The GEN-SPQ ablation: dense Count Table + bucket k-selection (same
+    results).  want_info=False skips the statistics (and their synchronisation)."""
     lib = load()
-    info = SpqInfo()
+    info = SpqInfo() if want_info else None
     opts = SpqOpts(buckets=buckets, max_bytes=max_bytes)
     _check(lib.genie_search_spq(index.handle, queries.handle, k, _ptr(d_k), ctypes.byref(opts),
-                                _ptr(d_ids), _ptr(d_counts), _ptr(d_n_valid), ctypes.byref(info),
+                                _ptr(d_ids), _ptr(d_counts), _ptr(d_n_valid),
+                                ctypes.byref(info) if info is not None else None,
                                 _stream(stream)), lib)
     return info
 

@@ -30,9 +30,10 @@ def u32(t: torch.Tensor) -> np.ndarray:
     return t.cpu().numpy().view(np.uint32)
 
 
-def build_index(w, chunk_shift: int = 0, stream=None) -> genie.Index:
+def build_index(w, chunk_shift: int = 0, stream=None, dense_min_df=None) -> genie.Index:
     off, kw = to_dev(w.obj_off), to_dev(w.obj_kw)
-    idx = genie.genie_build_index(off, kw, w.n_objects, w.vocab, chunk_shift, stream)
+    idx = genie.genie_build_index(off, kw, w.n_objects, w.vocab, chunk_shift, stream,
+                                  dense_min_df=dense_min_df)
     return idx
 
 

@@ -59,5 +59,12 @@ def test_opts_struct_layout_matches_header():
     # genie_search_opts: pointer, 4 x uint32, 2 pointers, host pointer, 2 events, flags (+pad)
     import ctypes
     assert ctypes.sizeof(genie.SearchOpts) == 8 + 4 * 4 + 8 * 3 + 8 * 2 + 8
-    assert ctypes.sizeof(genie.IndexInfo) == 40
-    assert ctypes.sizeof(genie.QueriesInfo) == 24
+    # genie_index_info: 2 x uint32, uint64, 4 x uint32, uint64, 2 x uint32, uint64
+    assert ctypes.sizeof(genie.IndexInfo) == 56
+    assert ctypes.sizeof(genie.IndexOpts) == 8
+    assert ctypes.sizeof(genie.QueriesInfo) == 32
+    # genie_server_opts / stats, genie_spq_opts / info, genie_calibration
+    assert ctypes.sizeof(genie.ServerOpts) == 8 + 6 * 4
+    assert ctypes.sizeof(genie.ServerStats) == 10 * 8
+    assert ctypes.sizeof(genie.SpqOpts) == 16 and ctypes.sizeof(genie.SpqInfo) == 32
+    assert ctypes.sizeof(genie.Calibration) == 8 + 8 + 8 * 4

@@ -137,7 +137,7 @@ def test_search_shape_reports_the_automatic_choice():
     qs = runner.compile_queries(idx, w)
     sh = genie.genie_search_shape(idx, qs, 10)
     assert (sh.counter_bits, sh.threads, sh.unroll) == (16, 1024, 2)
-    assert sh.kernel_name() == "scan_cpq_kernel<4, 2, 1024>"
+    assert sh.kernel_name() == "scan_cpq_kernel<4, 2, 1024, %s>" % ("true" if sh.dense else "false")
     blocks = genie.make_opts()
     runner.search(idx, qs, 10, opts=blocks)
     torch.cuda.synchronize()
@@ -444,3 +444,105 @@ def test_calibration_measures_a_positive_atomic_rate():
     cal = genie.genie_calibrate()
     assert cal.sms >= 1 and cal.seconds > 0
     assert 1e9 < cal.smem_atomics_per_s < 1e14
+
+
+# ---------------------------------------------------------------------------
+# dense keywords: object bitmaps added whole instead of their lists scanned
+# ---------------------------------------------------------------------------
+
+def _index_info(idx):
+    return idx.info
+
+
+@pytest.mark.parametrize("maker,k", [
+    (lambda: synth.lsh(150_000, 40, 100, config=51), 100),                       # 16-bit lanes
+    (lambda: synth.sets(120_000, (16, 200), 1 << 12, 48, (8, 300), 10, config=52), 10),
+    (lambda: synth.sets(90_000, (8, 40), 2000, 40, (4, 60), 25, config=53), 25),  # 8-bit lanes
+    (lambda: synth.relational(n_objects=60_000, values_per_dim=16, n_queries=32, config=54), 10)])
+def test_dense_bitmaps_give_the_counts_of_the_lists(maker, k):
+    """The default index stores dense keywords also as bitmaps; a search adds
+    them whole.  Results equal the index without bitmaps, the search told to
+    scan every list, and the oracle; the statistics show bitmaps were added."""
+    w = maker()
+    dense = runner.build_index(w)
+    plain = runner.build_index(w, dense_min_df=genie.GENIE_NO_DENSE)
+    assert dense.info.dense_keywords > 0 and plain.info.dense_keywords == 0
+    assert dense.info.dense_min_df == max(64, (w.n_objects + 31) // 32)
+    qd, qp = runner.compile_queries(dense, w), runner.compile_queries(plain, w)
+    st = torch.zeros(8, dtype=torch.int64, device="cuda")
+    a = runner.search(dense, qd, k, opts=genie.make_opts(d_stats=st,
+                                                         flags=genie.GENIE_SEARCH_DENSE)).host()
+    b = runner.search(plain, qp, k).host()
+    c = runner.search(dense, qd, k, opts=genie.make_opts(flags=genie.GENIE_SEARCH_NO_DENSE)).host()
+    d = runner.search(dense, qd, k).host()  # the library's own choice
+    torch.cuda.synchronize()
+    assert int(st[7].item()) > 0
+    for x in ("ids", "counts", "n_valid"):
+        assert np.array_equal(a[x], b[x]) and np.array_equal(a[x], c[x])
+        assert np.array_equal(a[x], d[x])
+    assert_same(a, oracle.topk(w, k=k))
+
+
+@pytest.mark.parametrize("min_df,shift", [(1, 0), (1, 13), (40, 14)])
+def test_every_keyword_dense_and_long_queries(min_df, shift):
+    """Bitmaps for (almost) every keyword: queries with more than 255 (and
+    more than 1024) dense keywords take several batches of adders; ranges of
+    every width; per-query k."""
+    w = synth.sets(70_001, (60, 240), 1500, 16, (300, 1200), 10, config=55)
+    rng = np.random.default_rng(5)
+    w.k = np.array([1, 10, 37], dtype=np.uint32)[rng.integers(0, 3, w.n_queries)]
+    idx = runner.build_index(w, 13, dense_min_df=min_df)
+    assert idx.info.dense_keywords > 0
+    res, _, qs = run(w, index=idx, opts=genie.make_opts(block_shift=shift,
+                                                         flags=genie.GENIE_SEARCH_DENSE))
+    assert_same(res, oracle.topk(w))
+
+
+def test_dense_gate_state_per_range():
+    """With bitmaps and every range running the Gate from AT = 1, the
+    ZipperArray set from the bitmap counts keeps Theorem 3.1: AT_f - 1 is each
+    range's k-th count; and 8-bit lanes without headroom (B = 200)."""
+    for w, shift in ((synth.lsh(50_000, 12, 20, config=17), 13),
+                     (synth.sets(50_000, (100, 290), 300, 10, (200, 200), 10, config=56), 14)):
+        idx = runner.build_index(w, 12, dense_min_df=100)
+        assert idx.info.dense_keywords > 0
+        qs = runner.compile_queries(idx, w)
+        groups = (w.n_objects + (1 << shift) - 1) >> shift
+        at = torch.zeros(w.n_queries * groups, dtype=torch.int32, device="cuda")
+        opts = genie.make_opts(block_shift=shift, d_chunk_at=at,
+                               flags=genie.GENIE_SEARCH_PER_RANGE_AT | genie.GENIE_SEARCH_DENSE)
+        res = runner.search(idx, qs, w.k, opts=opts).host()
+        at = runner.u32(at).reshape(w.n_queries, groups)
+        assert_same(res, oracle.topk(w))
+        for g in range(groups):
+            lo, hi = g << shift, min(w.n_objects, (g + 1) << shift)
+            ref = oracle.topk(w, obj_range=(lo, hi))
+            assert np.array_equal(at[:, g] - 1, ref["tk"]), g
+
+
+def test_dense_with_seeds_batch_and_noalloc():
+    """The seeded search (verify and rerun), the persistent batch and the
+    no-alloc entry point all add bitmaps the same way."""
+    w = synth.lsh(120_000, 64, 50, config=57)
+    idx = runner.build_index(w, dense_min_df=1500)
+    assert idx.info.dense_keywords > 0
+    qs = runner.compile_queries(idx, w)
+    ref = oracle.topk(w)
+    seeds = np.maximum(1, ref["tk"].astype(np.int64) - np.arange(w.n_queries) % 3)
+    seeds[::7] += 5  # some seeds above the k-th count: those queries rerun
+    st = torch.zeros(8, dtype=torch.int64, device="cuda")
+    res = runner.search(idx, qs, 50, opts=genie.make_opts(
+        d_seed=runner.to_dev(seeds.astype(np.uint32)), d_stats=st,
+        flags=genie.GENIE_SEARCH_DENSE)).host()
+    torch.cuda.synchronize()
+    assert_same(res, ref)
+    assert int(st[3].item()) > 0
+    batch = genie.Batch(idx, w.n_queries, qs.max_bound, 50, None)
+    out = runner.Outputs(w.n_queries, 50)
+    batch.run(qs, out.ids, out.counts, out.n_valid)
+    torch.cuda.synchronize()
+    assert_same(out.host(), ref)
+    out2 = runner.Outputs(w.n_queries, 50)
+    genie.genie_search_noalloc(idx, qs, 50, out2.ids, out2.counts, out2.n_valid)
+    torch.cuda.synchronize()
+    assert_same(out2.host(), ref)
