@@ -446,7 +446,7 @@ __device__ __noinline__ void ht_insert(const GateState g, uint32_t id, uint32_t 
   g.flags[0] = 1;  // not placed: the read-out falls back to the Bitmap Counter
 }
 
-// AT advance of Algorithm 1 (lines 5-6): while ZA[AT] >= k, AT grows by one.
+// AT advance of Algorithm 1: while ZA[AT] >= k, AT grows by one.
 // AT is read without locking and raised by atomicMax, so concurrent callers
 // only ever move it up to a level whose ZipperArray entry has reached k.
 __device__ __noinline__ void advance_at(const GateState g, uint32_t kq, uint32_t B) {
@@ -457,7 +457,7 @@ __device__ __noinline__ void advance_at(const GateState g, uint32_t kq, uint32_t
   }
 }
 
-// The Gate of Algorithm 1 (lines 3-7) for one posting that made object id's
+// The Gate of Algorithm 1 for one posting that made object id's
 // count c >= AT: the pass is numbered z at its level by the ZipperArray
 // increment; the first k passes of a level are hash-table candidates (each
 // object inserted once while it holds its presence bit); the pass that fills
@@ -839,7 +839,12 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     // next tile is located and loaded into the same registers while the
     // updates are in flight.  The Gate test needs the counts only, not the
     // ids; the rare tile that passes it reloads its ids (from L1).
-    uint32_t run = warp, t = run * kRun, t_end = min(t + kRun, total_tiles);
+    // Runs of kRun tiles, except the last 2 x nwarps tiles of the round,
+    // which are runs of one tile: the warps finish the round more evenly.
+    const uint32_t n_big = total_tiles > 2 * nwarps ? (total_tiles - 2 * nwarps) / kRun : 0u;
+    auto run_first = [&](uint32_t r) { return r < n_big ? r * kRun : n_big * kRun + (r - n_big); };
+    auto run_last = [&](uint32_t r, uint32_t f) { return min(f + (r < n_big ? kRun : 1u), total_tiles); };
+    uint32_t run = warp, t = run_first(run), t_end = run_last(run, t);
     uint32_t lo = 0, hi = 0, start = 0;
     uint4 v[kUnroll];
 #pragma unroll
@@ -856,10 +861,10 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
         if (lane == 0) r = atomicAdd(&S.next_run, 1u);
         run = __shfl_sync(0xFFFFFFFFu, r, 0);
       }
-      const uint32_t tn = run_ends ? run * kRun : t + 1;
-      const uint32_t tn_end = run_ends ? min(tn + kRun, total_tiles) : t_end;
-      // Bitmap Counter: one sub-word atomic add per posting (Algorithm 1,
-      // lines 1-2); val = the counter word before the add (0 for slots
+      const uint32_t tn = run_ends ? run_first(run) : t + 1;
+      const uint32_t tn_end = run_ends ? run_last(run, tn) : t_end;
+      // Bitmap Counter: one sub-word atomic add per posting (the count update
+      // of Algorithm 1); val = the counter word before the add (0 for slots
       // outside the list).  Every id of a sublist lies in this block's range.
       uint32_t val[4 * kUnroll];
       if (gateless) {  // counting only: no old value is needed
@@ -890,7 +895,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
                                       Lane<LOG2W>::inc(id));
         }
       }
-      // Gate (Algorithm 1, lines 3-7) for the postings whose new count reaches
+      // Gate (Algorithm 1) for the postings whose new count reaches
       // the (possibly stale) AuditThreshold: rare, so a tile is tested once.
       // With headroom (every count below the lanes' top bit) the test runs
       // on whole words: adding 2^(W-1) - (AT - 1) to every lane sets a lane's

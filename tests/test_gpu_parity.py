@@ -237,6 +237,34 @@ def test_index_is_the_transpose_of_the_objects():
     assert idx.max_object_len == int(np.diff(w.obj_off.astype(np.int64)).max())
 
 
+@pytest.mark.parametrize("vocab", [1, 2, 256, 257, 70_001, 1 << 25])
+def test_index_transpose_every_digit_count(vocab):
+    """The 8-bit radix build for vocabularies of 0 to 4 digit passes (the last
+    one partial), hot keywords that fill whole warps with one digit, and a
+    ragged last tile: lists equal a stable sort of the pairs by keyword."""
+    rng = np.random.default_rng(vocab)
+    n = 23_457
+    lens = rng.integers(0, min(vocab, 40) + 1, n)
+    hot = rng.integers(0, vocab, 3)
+    objs = []
+    for L in lens:
+        kw = np.concatenate([hot[: rng.integers(0, 4)], rng.integers(0, vocab, L)])
+        objs.append(np.unique(kw)[:max(int(L), 1)] if L else kw[:0])
+    obj_off = np.concatenate([[0], np.cumsum([len(o) for o in objs])]).astype(np.uint32)
+    obj_kw = np.concatenate(objs).astype(np.uint32)
+    w = synth.Workload("radix", "keywords", n, vocab, obj_off, obj_kw, 1, 1,
+                       q_off=np.array([0, 1], dtype=np.uint32), q_kw=obj_kw[:1].copy())
+    idx = runner.build_index(w)
+    kw_off = torch.empty(vocab + 1, dtype=torch.int64, device="cuda")
+    post = torch.empty(max(w.nnz, 1), dtype=torch.int32, device="cuda")
+    genie.genie_index_export(idx, kw_off, post)
+    owner = np.repeat(np.arange(n, dtype=np.uint32), np.diff(obj_off.astype(np.int64)))
+    order = np.argsort(obj_kw, kind="stable")
+    want_off = np.concatenate([[0], np.cumsum(np.bincount(obj_kw, minlength=vocab))])
+    assert np.array_equal(kw_off.cpu().numpy(), want_off)
+    assert np.array_equal(runner.u32(post)[: w.nnz], owner[order])
+
+
 # ---------------------------------------------------------------------------
 # edge cases
 # ---------------------------------------------------------------------------
@@ -546,3 +574,26 @@ def test_dense_with_seeds_batch_and_noalloc():
     genie.genie_search_noalloc(idx, qs, 50, out2.ids, out2.counts, out2.n_valid)
     torch.cuda.synchronize()
     assert_same(out2.host(), ref)
+
+
+def test_dense_instantiation_chosen_for_zipf_sets_in_search_and_batch():
+    """Where dense keywords carry most of a batch's postings (Zipf sets), the
+    search and the persistent batch both add their bitmaps (the dense
+    instantiation and graph), and the results stay the oracle's."""
+    w = synth.sets(150_000, (16, 200), 1 << 12, 64, (8, 300), 10, config=58)
+    idx = runner.build_index(w)
+    qs = runner.compile_queries(idx, w)
+    qi = genie.QueriesInfo()
+    genie.load().genie_queries_get_info(qs.handle, genie.ctypes.byref(qi))
+    assert 2 * qi.n_dense_entries >= qi.n_entries > 0
+    assert genie.genie_search_shape(idx, qs, 10).dense == 1
+    ref = oracle.topk(w)
+    st = torch.zeros(8, dtype=torch.int64, device="cuda")
+    assert_same(runner.search(idx, qs, 10, opts=genie.make_opts(d_stats=st)).host(), ref)
+    assert int(st[7].item()) > 0
+    batch = genie.Batch(idx, w.n_queries, qs.max_bound, 10, None)
+    out = runner.Outputs(w.n_queries, 10)
+    for _ in range(2):  # a replayed graph starts from a clean state
+        batch.run(qs, out.ids, out.counts, out.n_valid)
+        torch.cuda.synchronize()
+        assert_same(out.host(), ref)
