@@ -3,10 +3,13 @@
 //
 // The paper builds its index on the CPU (Table 2, "Index-build").  Here the
 // transposition object -> keywords into keyword -> objects is a stable LSD
-// radix sort of the (keyword, object id) pairs by keyword, one bit per pass
-// (count zeros per tile, scan the tile counts, scatter).  The pairs enter in
-// ascending object id, so stability leaves every postings list in ascending id
-// order, which the block-per-object-range scan depends on.
+// radix sort of the (keyword, object id) pairs by keyword, eight bits per pass
+// (three passes for a vocabulary of up to 2^24): per tile a 256-bin digit
+// histogram, one exclusive scan over the (digit, tile) counts, and a scatter
+// that ranks each pair among the tile's pairs with the same digit in input
+// order.  The pairs enter in ascending object id, so stability leaves every
+// postings list in ascending id order, which the block-per-object-range scan
+// depends on.
 #include <algorithm>
 #include <cstdio>
 #include <vector>
@@ -17,9 +20,18 @@
 namespace genie {
 namespace {
 
-constexpr uint32_t kSplitThreads = 256;
-constexpr uint32_t kSplitItems = 16;
-constexpr uint32_t kSplitTile = kSplitThreads * kSplitItems;
+// Radix tiles: 256 threads (one per digit value) x 16 pairs; each warp ranks
+// a contiguous 512 pairs of the tile.
+constexpr uint32_t kRadixBits = 8;
+constexpr uint32_t kDigits = 1u << kRadixBits;
+constexpr uint32_t kRadixThreads = kDigits;
+constexpr uint32_t kRadixItems = 16;
+constexpr uint32_t kRadixTile = kRadixThreads * kRadixItems;
+constexpr uint32_t kRadixWarps = kRadixThreads / 32;
+// Large exclusive scans: blocks of 256 threads x 16 values.
+constexpr uint32_t kScanThreads = 256;
+constexpr uint32_t kScanItems = 16;
+constexpr uint32_t kScanChunk = kScanThreads * kScanItems;
 
 enum BuildFlag { kBadOffsets = 0, kBadKeyword = 1, kMaxLen = 2, kDuplicate = 3, kNumFlags = 4 };
 
@@ -57,19 +69,56 @@ __global__ void expand_pairs_kernel(const uint32_t* __restrict__ off, const uint
   }
 }
 
-// zeros of bit `bit` per tile of kSplitTile keys
-__global__ void split_count_kernel(const uint32_t* __restrict__ keys, uint32_t n, int bit,
-                                   uint32_t* __restrict__ tile_zeros) {
-  __shared__ uint32_t scratch[33];
-  uint64_t start = (uint64_t)blockIdx.x * kSplitTile;
-  uint32_t z = 0;
+// Digit histogram of each tile: tile_hist[d * n_tiles + tile] = pairs of the
+// tile whose key has digit d at `shift` (d < nd; larger digits do not occur).
+__global__ void radix_count_kernel(const uint32_t* __restrict__ keys, uint32_t n, uint32_t shift,
+                                   uint32_t nd, uint32_t n_tiles, uint32_t* __restrict__ tile_hist) {
+  __shared__ uint32_t h[kDigits];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t start = (uint64_t)blockIdx.x * kRadixTile;
 #pragma unroll
-  for (uint32_t j = 0; j < kSplitItems; ++j) {
-    uint64_t i = start + j * kSplitThreads + threadIdx.x;
-    if (i < n) z += ((keys[i] >> bit) & 1u) ^ 1u;
+  for (uint32_t j = 0; j < kRadixItems; ++j) {
+    const uint64_t i = start + j * kRadixThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & (kDigits - 1)], 1u);
   }
-  uint32_t total = dev::block_sum(z, scratch);
-  if (threadIdx.x == 0) tile_zeros[blockIdx.x] = total;
+  __syncthreads();
+  if (threadIdx.x < nd) tile_hist[(uint64_t)threadIdx.x * n_tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Sums of consecutive chunks of kScanChunk values (first phase of a scan).
+__global__ void scan_partial_kernel(const uint32_t* __restrict__ v, uint64_t n,
+                                    uint32_t* __restrict__ part) {
+  __shared__ uint32_t scratch[33];
+  const uint64_t start = (uint64_t)blockIdx.x * kScanChunk;
+  uint32_t s = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < kScanItems; ++j) {
+    const uint64_t i = start + j * kScanThreads + threadIdx.x;
+    if (i < n) s += v[i];
+  }
+  const uint32_t total = dev::block_sum(s, scratch);
+  if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+// Exclusive scan of each chunk in place, offset by the chunk's scanned sum.
+__global__ void scan_apply_kernel(uint32_t* __restrict__ v, uint64_t n,
+                                  const uint32_t* __restrict__ part) {
+  __shared__ uint32_t scratch[33];
+  const uint64_t mine = (uint64_t)blockIdx.x * kScanChunk + (uint64_t)threadIdx.x * kScanItems;
+  uint32_t x[kScanItems], s = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < kScanItems; ++j) {
+    x[j] = mine + j < n ? v[mine + j] : 0u;
+    s += x[j];
+  }
+  uint32_t tot;
+  uint32_t base = part[blockIdx.x] + dev::block_exclusive_scan(s, scratch, &tot);
+#pragma unroll
+  for (uint32_t j = 0; j < kScanItems; ++j) {
+    if (mine + j < n) v[mine + j] = base;
+    base += x[j];
+  }
 }
 
 }  // namespace
@@ -97,36 +146,63 @@ void launch_exclusive_scan(uint32_t* v, uint32_t n, uint32_t* total, cudaStream_
 
 namespace {
 
-// stable split by bit: zeros first, then ones, each in input order
-__global__ void split_scatter_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
-                                     uint32_t n, int bit, const uint32_t* __restrict__ tile_zero_base,
-                                     const uint32_t* __restrict__ total_zeros,
+// Stable scatter of one tile by the digit at `shift`.  A pair's destination
+// is tile_off[d * n_tiles + tile] (the pairs of digit d in earlier tiles and
+// of smaller digits everywhere, from the scan of the histograms) plus the
+// pairs of digit d before it in the tile.  Warp w ranks the tile's pairs
+// [512 w, 512 w + 512) in 16 rounds of 32 consecutive pairs: the lanes that
+// share a digit in a round find each other with match.any, take their order
+// from their lane numbers and their base from the warp's running count of the
+// digit; the counts of the warps before it are added afterwards.
+__global__ void radix_scatter_kernel(const uint32_t* __restrict__ keys,
+                                     const uint32_t* __restrict__ vals, uint32_t n, uint32_t shift,
+                                     uint32_t nd, uint32_t n_tiles,
+                                     const uint32_t* __restrict__ tile_off,
                                      uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
-  __shared__ uint32_t scratch[33];
-  const uint64_t tile_start = (uint64_t)blockIdx.x * kSplitTile;
-  const uint64_t my = tile_start + (uint64_t)threadIdx.x * kSplitItems;
-  uint32_t k[kSplitItems], v[kSplitItems];
-  uint32_t z = 0;
+  __shared__ uint32_t wh[kRadixWarps][kDigits];
+  const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 #pragma unroll
-  for (uint32_t j = 0; j < kSplitItems; ++j) {
-    bool ok = my + j < n;
-    k[j] = ok ? keys[my + j] : 0xFFFFFFFFu;
-    v[j] = ok ? vals[my + j] : 0u;
-    if (ok) z += ((k[j] >> bit) & 1u) ^ 1u;
+  for (uint32_t w = 0; w < kRadixWarps; ++w) wh[w][tid] = 0;
+  __syncthreads();
+  const uint64_t wbase = (uint64_t)blockIdx.x * kRadixTile + warp * (32u * kRadixItems);
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t k[kRadixItems], v[kRadixItems], r[kRadixItems];
+#pragma unroll
+  for (uint32_t j = 0; j < kRadixItems; ++j) {
+    const uint64_t i = wbase + j * 32 + lane;
+    const bool ok = i < n;
+    k[j] = ok ? keys[i] : 0u;
+    v[j] = ok ? vals[i] : 0u;
+    const uint32_t d = ok ? (k[j] >> shift) & (kDigits - 1) : kDigits;  // kDigits: no pair
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+    const uint32_t leader = __ffs(peers) - 1;
+    uint32_t before = 0;
+    if (ok && lane == leader) {
+      before = wh[warp][d];
+      wh[warp][d] = before + __popc(peers);
+    }
+    r[j] = __shfl_sync(0xFFFFFFFFu, before, leader) + __popc(peers & lt);
+    __syncwarp();
   }
-  uint32_t tot;
-  uint32_t zbefore = dev::block_exclusive_scan(z, scratch, &tot);
-  const uint32_t zbase = tile_zero_base[blockIdx.x];
-  const uint32_t tz = *total_zeros;
-  // ones before this thread in the tile = items before it - zeros before it
-  uint32_t obase = tz + (uint32_t)(tile_start - zbase) + threadIdx.x * kSplitItems - zbefore;
-  uint32_t zi = zbase + zbefore;
+  __syncthreads();
+  // thread d: pairs of digit d in the warps before each warp, plus the base
+  if (tid < nd) {
+    uint32_t run = tile_off[(uint64_t)tid * n_tiles + blockIdx.x];
 #pragma unroll
-  for (uint32_t j = 0; j < kSplitItems; ++j) {
-    if (my + j >= n) break;
-    uint32_t dst = ((k[j] >> bit) & 1u) ? obase++ : zi++;
-    keys_out[dst] = k[j];
-    vals_out[dst] = v[j];
+    for (uint32_t w = 0; w < kRadixWarps; ++w) {
+      const uint32_t c = wh[w][tid];
+      wh[w][tid] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (uint32_t j = 0; j < kRadixItems; ++j) {
+    if (wbase + j * 32 + lane < n) {
+      const uint32_t dst = wh[warp][(k[j] >> shift) & (kDigits - 1)] + r[j];
+      keys_out[dst] = k[j];
+      vals_out[dst] = v[j];
+    }
   }
 }
 
@@ -257,10 +333,16 @@ extern "C" genie_status genie_build_index_ex(const uint32_t* d_obj_off, const ui
   GENIE_CUDA_TRY(cudaMalloc(&keys_b.p, std::max<uint64_t>(nnz, 1) * 4));
   GENIE_CUDA_TRY(cudaMalloc(&vals_a.p, padded * 4));
   GENIE_CUDA_TRY(cudaMalloc(&vals_b.p, padded * 4));
-  const uint32_t n_tiles = (uint32_t)((nnz + kSplitTile - 1) / kSplitTile);
-  GENIE_CUDA_TRY(cudaMalloc(&tiles_b.p, (uint64_t)(n_tiles + 2) * 4));
-  uint32_t* tile_zeros = (uint32_t*)tiles_b.p;
-  uint32_t* total_zeros = tile_zeros + n_tiles + 1;
+  int bits = 0;
+  while (bits < 32 && ((uint64_t)1 << bits) < vocab) ++bits;
+  const uint32_t n_tiles = (uint32_t)((nnz + kRadixTile - 1) / kRadixTile);
+  const uint32_t max_nd = (uint32_t)std::min<uint64_t>(kDigits, (uint64_t)1 << bits);
+  const uint64_t hist_n = (uint64_t)max_nd * n_tiles;
+  const uint32_t n_parts = (uint32_t)((hist_n + kScanChunk - 1) / kScanChunk);
+  GENIE_CUDA_TRY(cudaMalloc(&tiles_b.p, (hist_n + n_parts + 2) * 4));
+  uint32_t* tile_hist = (uint32_t*)tiles_b.p;
+  uint32_t* parts = tile_hist + hist_n;
+  uint32_t* parts_total = parts + n_parts + 1;
 
   uint32_t *ka = (uint32_t*)keys_a.p, *kb = (uint32_t*)keys_b.p;
   uint32_t *va = (uint32_t*)vals_a.p, *vb = (uint32_t*)vals_b.p;
@@ -268,13 +350,16 @@ extern "C" genie_status genie_build_index_ex(const uint32_t* d_obj_off, const ui
     expand_pairs_kernel<<<grid_for((uint64_t)n_objects * 32, 256), 256, 0, s>>>(d_obj_off, d_obj_kw,
                                                                                n_objects, ka, va);
     GENIE_CUDA_TRY(cudaGetLastError());
-    int bits = 0;
-    while (bits < 32 && ((uint64_t)1 << bits) < vocab) ++bits;
-    for (int bit = 0; bit < bits; ++bit) {
-      split_count_kernel<<<n_tiles, kSplitThreads, 0, s>>>(ka, nnz, bit, tile_zeros);
-      scan_small_kernel<<<1, 1024, 0, s>>>(tile_zeros, n_tiles, total_zeros);
-      split_scatter_kernel<<<n_tiles, kSplitThreads, 0, s>>>(ka, va, nnz, bit, tile_zeros,
-                                                              total_zeros, kb, vb);
+    for (uint32_t shift = 0; shift < (uint32_t)bits; shift += kRadixBits) {
+      const uint32_t nd = 1u << std::min<uint32_t>(kRadixBits, (uint32_t)bits - shift);
+      const uint64_t hn = (uint64_t)nd * n_tiles;
+      const uint32_t np = (uint32_t)((hn + kScanChunk - 1) / kScanChunk);
+      radix_count_kernel<<<n_tiles, kRadixThreads, 0, s>>>(ka, nnz, shift, nd, n_tiles, tile_hist);
+      scan_partial_kernel<<<np, kScanThreads, 0, s>>>(tile_hist, hn, parts);
+      scan_small_kernel<<<1, 1024, 0, s>>>(parts, np, parts_total);
+      scan_apply_kernel<<<np, kScanThreads, 0, s>>>(tile_hist, hn, parts);
+      radix_scatter_kernel<<<n_tiles, kRadixThreads, 0, s>>>(ka, va, nnz, shift, nd, n_tiles,
+                                                             tile_hist, kb, vb);
       GENIE_CUDA_TRY(cudaGetLastError());
       std::swap(ka, kb);
       std::swap(va, vb);
