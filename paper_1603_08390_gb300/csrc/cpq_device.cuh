@@ -839,9 +839,9 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     // next tile is located and loaded into the same registers while the
     // updates are in flight.  The Gate test needs the counts only, not the
     // ids; the rare tile that passes it reloads its ids (from L1).
-    // Runs of kRun tiles, except the last 2 x nwarps tiles of the round,
+    // Runs of kRun tiles, except the last 4 x nwarps tiles of the round,
     // which are runs of one tile: the warps finish the round more evenly.
-    const uint32_t n_big = total_tiles > 2 * nwarps ? (total_tiles - 2 * nwarps) / kRun : 0u;
+    const uint32_t n_big = total_tiles > 4 * nwarps ? (total_tiles - 4 * nwarps) / kRun : 0u;
     auto run_first = [&](uint32_t r) { return r < n_big ? r * kRun : n_big * kRun + (r - n_big); };
     auto run_last = [&](uint32_t r, uint32_t f) { return min(f + (r < n_big ? kRun : 1u), total_tiles); };
     uint32_t run = warp, t = run_first(run), t_end = run_last(run, t);
@@ -1199,13 +1199,20 @@ genie_status make_plan(const genie_index* idx, const genie_queries* qs, uint32_t
   if (slots & (slots - 1)) return fail(GENIE_ERR_INVALID_ARG, "genie_search: ht_slots must be a power of two");
   if (slots < 32) return fail(GENIE_ERR_INVALID_ARG, "genie_search: ht_slots must be >= 32");
   p->ht_slots = slots;
+  // Dense keywords' bitmaps pay when they carry most of the batch's postings
+  // (their instantiation of the scan is slower on the lists it still scans).
+  p->dense = idx->n_dense && p->log2w >= 3 && !(o && (o->flags & GENIE_SEARCH_NO_DENSE)) &&
+             ((o && (o->flags & GENIE_SEARCH_DENSE)) ||
+              (2 * qs->n_dense_entries >= qs->n_entries && qs->n_dense_entries > 0));
   // Default shape from the mean sublist a block scans per keyword: long
   // sublists go faster with fewer, wider warps (eight 16-byte loads per lane
   // in flight, less tile bookkeeping per posting), short ones with more warps
   // and smaller tiles (less waste at the sublist ends): 1024 threads, whose
   // 64 registers the loop fits, except with 4-bit counters, whose lane
   // arithmetic needs the registers of 768.
-  const double seg = qs->n_keywords ? (double)qs->n_entries / ((double)qs->n_keywords * p->n_groups) : 0.0;
+  // (postings of dense keywords are not scanned when their bitmaps are added)
+  const uint64_t scanned = qs->n_entries - (p->dense ? qs->n_dense_entries : 0);
+  const double seg = qs->n_keywords ? (double)scanned / ((double)qs->n_keywords * p->n_groups) : 0.0;
   const uint32_t short_threads = p->log2w >= 3 ? 1024u : 768u;
   p->threads = (o && o->threads) ? o->threads : (seg >= kLongSublist ? 512u : short_threads);
   if (p->threads != 512 && p->threads != 768 && p->threads != 896 && p->threads != 1024)
@@ -1216,11 +1223,6 @@ genie_status make_plan(const genie_index* idx, const genie_queries* qs, uint32_t
   if (p->threads == 512 ? (p->unroll != 4 && p->unroll != 8) : (p->unroll != 2 && p->unroll != 4))
     return fail(GENIE_ERR_INVALID_ARG, "genie_search: unroll must be 2 or 4 (768 or 1024 threads), 4 or 8 (512)");
   p->za_len = B + 2;
-  // Dense keywords' bitmaps pay when they carry most of the batch's postings
-  // (their instantiation of the scan is slower on the lists it still scans).
-  p->dense = idx->n_dense && p->log2w >= 3 && !(o && (o->flags & GENIE_SEARCH_NO_DENSE)) &&
-             ((o && (o->flags & GENIE_SEARCH_DENSE)) ||
-              (2 * qs->n_dense_entries >= qs->n_entries && qs->n_dense_entries > 0));
   p->smem = scan_smem_bytes(p->log2w, shift, slots, p->za_len, k);
   int dev = 0, max_smem = 0;
   cudaGetDevice(&dev);

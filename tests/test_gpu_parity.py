@@ -148,12 +148,18 @@ def test_search_shape_reports_the_automatic_choice():
     with pytest.raises(genie.GenieError) as e:
         genie.genie_search_shape(idx, qs, 10, genie.make_opts(threads=896, unroll=4))
     assert e.value.status == genie.GENIE_ERR_INVALID_ARG
-    # long sublists (a small vocabulary): 512 threads, eight loads per lane
+    # long sublists (a small vocabulary, no bitmaps): 512 threads, eight loads per lane
     w = synth.sets(50_000, (100, 290), 300, 8, (128, 128), 10, config=201)
+    idx = runner.build_index(w, dense_min_df=genie.GENIE_NO_DENSE)
+    qs = runner.compile_queries(idx, w)
+    sh = genie.genie_search_shape(idx, qs, 10)
+    assert (sh.counter_bits, sh.threads, sh.unroll, sh.dense) == (8, 512, 8, 0)
+    # the same lists as bitmaps: nothing long is left to scan, so the short shape
     idx = runner.build_index(w)
     qs = runner.compile_queries(idx, w)
     sh = genie.genie_search_shape(idx, qs, 10)
-    assert (sh.counter_bits, sh.threads, sh.unroll) == (8, 512, 8)
+    assert (sh.counter_bits, sh.threads, sh.unroll, sh.dense) == (8, 1024, 2, 1)
+    assert_same(runner.search(idx, qs, 10).host(), oracle.topk(w))
     # 4-bit counters keep 768 threads for short sublists (3 items of 5 values: B = 15)
     w = synth.relational(n_objects=70_001, n_queries=8, config=11, items_per_query=3)
     idx = runner.build_index(w)
