@@ -3,15 +3,13 @@
 //
 // A batch of Q queries against an index split into G object ranges is Q x G
 // work items, each the c-PQ pass of one (query, range) (cpq_item).  One block
-// per SM pulls items from a device counter in a fixed order: range by range
-// (so that the blocks resident at one time share one range of the List Array
-// in L2), and inside a range the queries with the most postings first (a
-// longest-processing-time order, which keeps Zipf-heavy queries off the tail;
-// the paper splits long lists instead, Sec. 3.2.1).  When a block finishes the
-// last range of a query it merges that query's ranges right away (Sec. 3.4
-// merge on the device), so the whole batch is one kernel.  The order kernel
-// and the persistent kernel are captured once into a CUDA graph; each batch
-// rewrites a small descriptor in device memory and replays the graph.
+// per SM pulls items from a device counter range by range, so that the
+// blocks resident at one time share one range of the List Array in L2.  The
+// per-range top-k lists are merged by a second kernel (Sec. 3.4, on the
+// device).  Both launches are captured once into a CUDA graph; each batch
+// sets the kernels' arguments on the graph's nodes and replays it.  The
+// scan arguments are kernel parameters, as in the one-block-per-item search,
+// so an item runs the same code as in scan_cpq_kernel.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -28,76 +26,28 @@
 namespace genie {
 namespace {
 
-constexpr uint32_t kOrderCap = 16384;  // queries the order kernel sorts in one block
-
+// Per-batch arguments of the two captured kernels (set on their graph nodes).
 struct BatchDesc {
   ScanArgs scan;
   MergeArgs merge;
-  const uint64_t* entries;  // [n] postings per query
-  uint32_t* order;          // [max_queries] batch positions, heaviest first
-  uint32_t* work;           // next work item
-  uint32_t* done;           // [max_queries] finished ranges per query
 };
 
-// order[] = queries by postings scanned, descending (ties: lower position
-// first); identity for batches above kOrderCap
-__global__ void __launch_bounds__(1024) order_kernel(const BatchDesc* __restrict__ D) {
-  extern __shared__ uint4 smem_raw[];
-  unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw);
-  const uint32_t n = D->scan.n_sel;
-  if (n > kOrderCap) {
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) D->order[i] = i;
-    return;
-  }
-  const uint32_t n2 = dev::next_pow2(max(n, 1u));
-  for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) {
-    unsigned long long k = 0;
-    if (i < n) {
-      const unsigned long long cap = (1ull << 40) - 1;
-      const unsigned long long e = D->entries[i] < cap ? (unsigned long long)D->entries[i] : cap;
-      k = (e << 24) | (unsigned long long)(0xFFFFFFu - i);
-    }
-    keys[i] = k;
-  }
-  __syncthreads();
-  dev::bitonic_sort_desc(keys, n2);
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
-    D->order[i] = 0xFFFFFFu - (uint32_t)(keys[i] & 0xFFFFFFull);
-}
-
+// Persistent blocks: each pulls the next (query, range) item from *work until
+// the batch is done.
 template <int LOG2W, int U, int THREADS, bool DENSE>
-__global__ void __launch_bounds__(THREADS, 1) batch_cpq_kernel(const BatchDesc* __restrict__ D) {
+__global__ void __launch_bounds__(THREADS, 1)
+    batch_cpq_kernel(const __grid_constant__ ScanArgs SA, uint32_t* __restrict__ work) {
   extern __shared__ uint4 smem_raw[];
   __shared__ BlockShared S;
-  __shared__ MergeShared MS;
-  __shared__ ScanArgs SA;
-  __shared__ MergeArgs SM;
-  __shared__ uint32_t s_last;
-  if (threadIdx.x == 0) {
-    SA = D->scan;
-    SM = D->merge;
-  }
-  __syncthreads();
-  const uint32_t Q = SA.n_sel, G = SA.n_groups;
-  const uint32_t total = Q * G;
-  unsigned long long* buf = reinterpret_cast<unsigned long long*>(smem_raw);
-  uint32_t* hist = reinterpret_cast<uint32_t*>(buf + dev::next_pow2(SA.k));
+  const uint32_t Q = SA.n_sel;
+  const uint32_t total = Q * SA.n_groups;
   for (;;) {
-    if (threadIdx.x == 0) S.item = atomicAdd(D->work, 1u);
+    if (threadIdx.x == 0) S.item = atomicAdd(work, 1u);
     __syncthreads();
     const uint32_t item = S.item;
     if (item >= total) break;
     const uint32_t g = item / Q;
-    const uint32_t qi = D->order[item - g * Q];
-    cpq_item<LOG2W, U, DENSE>(SA, qi, g, smem_raw, S);
-    __threadfence();  // this item's candidate list, visible to the merging block
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&D->done[qi], 1u) == G - 1;
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      merge_query<true>(SM, qi, buf, hist, MS);
-    }
+    cpq_item<LOG2W, U, DENSE>(SA, item - g * Q, g, smem_raw, S);
     __syncthreads();
   }
 }
@@ -105,25 +55,25 @@ __global__ void __launch_bounds__(THREADS, 1) batch_cpq_kernel(const BatchDesc* 
 // launch = false only raises the kernel's shared-memory limit (done before a
 // stream capture begins)
 template <int LOG2W, int U, int THREADS>
-cudaError_t launch_batch(const BatchDesc* d, uint32_t blocks, size_t smem, cudaStream_t s,
-                         bool launch, bool dense) {
+cudaError_t launch_batch(uint32_t* work, const BatchDesc& args, uint32_t blocks, size_t smem,
+                         cudaStream_t s, bool launch, bool dense) {
   auto kern = (LOG2W >= 3 && dense) ? batch_cpq_kernel<LOG2W, U, THREADS, LOG2W >= 3>
                                     : batch_cpq_kernel<LOG2W, U, THREADS, false>;
   if (!launch) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kern<<<blocks, THREADS, smem, s>>>(d);
+  kern<<<blocks, THREADS, smem, s>>>(args.scan, work);
   return cudaGetLastError();
 }
 
 template <int LOG2W>
-cudaError_t batch_width(const BatchDesc* d, uint32_t blocks, size_t smem, uint32_t threads,
-                        uint32_t unroll, cudaStream_t s, bool launch, bool dense) {
-  if (threads == 512) return unroll == 8 ? launch_batch<LOG2W, 8, 512>(d, blocks, smem, s, launch, dense)
-                                         : launch_batch<LOG2W, 4, 512>(d, blocks, smem, s, launch, dense);
-  if (threads == 768) return unroll == 4 ? launch_batch<LOG2W, 4, 768>(d, blocks, smem, s, launch, dense)
-                                         : launch_batch<LOG2W, 2, 768>(d, blocks, smem, s, launch, dense);
-  if (threads == 896) return launch_batch<LOG2W, 2, 896>(d, blocks, smem, s, launch, dense);
-  return unroll == 4 ? launch_batch<LOG2W, 4, 1024>(d, blocks, smem, s, launch, dense)
-                     : launch_batch<LOG2W, 2, 1024>(d, blocks, smem, s, launch, dense);
+cudaError_t batch_width(uint32_t* d, const BatchDesc& args, uint32_t blocks, size_t smem,
+                        uint32_t threads, uint32_t unroll, cudaStream_t s, bool launch, bool dense) {
+  if (threads == 512) return unroll == 8 ? launch_batch<LOG2W, 8, 512>(d, args, blocks, smem, s, launch, dense)
+                                         : launch_batch<LOG2W, 4, 512>(d, args, blocks, smem, s, launch, dense);
+  if (threads == 768) return unroll == 4 ? launch_batch<LOG2W, 4, 768>(d, args, blocks, smem, s, launch, dense)
+                                         : launch_batch<LOG2W, 2, 768>(d, args, blocks, smem, s, launch, dense);
+  if (threads == 896) return launch_batch<LOG2W, 2, 896>(d, args, blocks, smem, s, launch, dense);
+  return unroll == 4 ? launch_batch<LOG2W, 4, 1024>(d, args, blocks, smem, s, launch, dense)
+                     : launch_batch<LOG2W, 2, 1024>(d, args, blocks, smem, s, launch, dense);
 }
 
 cudaError_t batch_dispatch(const genie_batch* b, bool launch);
@@ -156,15 +106,17 @@ struct genie_batch {
   bool dense = false;      // the instantiation being captured adds dense keywords' bitmaps
   bool can_dense = false;  // the index has object bitmaps: a second graph adds them
   size_t smem = 0;
-  genie::BatchDesc host_desc{};
-  genie::BatchDesc* desc = nullptr;
+  genie::BatchDesc host_desc{};  // the arguments' fixed part, as captured
   unsigned long long* cand = nullptr;
-  uint32_t* order = nullptr;
-  uint32_t* counters = nullptr;  // [0] work, [1 ..] done, [max_queries] seeds, histograms
+  uint32_t* counters = nullptr;  // [0] work, [1 ..] per-query seeds, then histograms
   uint64_t counter_words = 0;
   cudaStream_t capture_stream = nullptr;
   cudaGraph_t graph[2] = {nullptr, nullptr};      // [1]: dense keywords as bitmaps
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaGraphNode_t node[2] = {nullptr, nullptr};   // the persistent kernel's node of each graph
+  cudaKernelNodeParams node_params[2];            // its launch, as captured
+  cudaGraphNode_t mnode[2] = {nullptr, nullptr};  // the merge kernel's node
+  cudaKernelNodeParams mnode_params[2];
 };
 
 using namespace genie;
@@ -173,9 +125,9 @@ namespace genie {
 namespace {
 cudaError_t batch_dispatch(const genie_batch* b, bool launch) {
   cudaStream_t s = b->capture_stream;
-  return b->log2w == 2 ? batch_width<2>(b->desc, b->blocks, b->smem, b->threads, b->unroll, s, launch, b->dense)
-       : b->log2w == 3 ? batch_width<3>(b->desc, b->blocks, b->smem, b->threads, b->unroll, s, launch, b->dense)
-                       : batch_width<4>(b->desc, b->blocks, b->smem, b->threads, b->unroll, s, launch, b->dense);
+  return b->log2w == 2 ? batch_width<2>(b->counters, b->host_desc, b->blocks, b->smem, b->threads, b->unroll, s, launch, b->dense)
+       : b->log2w == 3 ? batch_width<3>(b->counters, b->host_desc, b->blocks, b->smem, b->threads, b->unroll, s, launch, b->dense)
+                       : batch_width<4>(b->counters, b->host_desc, b->blocks, b->smem, b->threads, b->unroll, s, launch, b->dense);
 }
 }  // namespace
 }  // namespace genie
@@ -188,9 +140,8 @@ void free_batch(genie_batch* b) {
     if (b->graph[i]) cudaGraphDestroy(b->graph[i]);
   }
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
-  cudaFree(b->desc);
   cudaFree(b->cand);
-  cudaFree(b->order);
+
   cudaFree(b->counters);
   delete b;
 }
@@ -242,15 +193,14 @@ extern "C" genie_status genie_batch_create(const genie_index* index, uint32_t ma
   b->blocks = (opts && opts->blocks) ? opts->blocks : (uint32_t)sms;
   const size_t merge_smem = (size_t)dev::next_pow2(k) * 8 + (size_t)p.za_len * 4;
   b->smem = std::max(b->smem, merge_smem);
-  cudaError_t e = cudaMalloc(&b->desc, sizeof(BatchDesc));
-  if (e == cudaSuccess) e = cudaMalloc(&b->cand, (uint64_t)max_queries * p.n_groups * k * 8);
-  if (e == cudaSuccess) e = cudaMalloc(&b->order, (uint64_t)max_queries * 4);
-  // work counter, per-query done counts and seeds, then per-query count
-  // histograms of the finished ranges (when they stay small)
+  cudaError_t e = cudaMalloc(&b->cand, (uint64_t)max_queries * p.n_groups * k * 8);
+  // work counter, per-query seeds, then per-query count histograms of the
+  // finished ranges (when they stay small)
   const uint64_t hist_words = (uint64_t)max_queries * p.za_len;
   const bool use_hist = hist_words * 4 <= kHintHistMaxBytes;
-  b->counter_words = 2 * (uint64_t)max_queries + 1 + (use_hist ? hist_words : 0);
+  b->counter_words = (uint64_t)max_queries + 1 + (use_hist ? hist_words : 0);
   if (e == cudaSuccess) e = cudaMalloc(&b->counters, b->counter_words * 4);
+
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     free_batch(b);
@@ -275,32 +225,50 @@ extern "C" genie_status genie_batch_create(const genie_index* index, uint32_t ma
   d.scan.ht_slots = p.ht_slots;
   d.scan.za_len = p.za_len;
   d.scan.cand = b->cand;
-  d.scan.at_hint = b->counters + 1 + max_queries;
-  d.scan.hint_hist = use_hist ? b->counters + 1 + 2 * (uint64_t)max_queries : nullptr;
+  d.scan.at_hint = b->counters + 1;
+  d.scan.hint_hist = use_hist ? b->counters + 1 + (uint64_t)max_queries : nullptr;
   d.scan.hint_stride = p.za_len;
   d.merge.cand = b->cand;
   d.merge.n_groups = p.n_groups;
   d.merge.k = k;
   d.merge.za_len = p.za_len;
-  d.order = b->order;
-  d.work = b->counters;
-  d.done = b->counters + 1;
-  // capture: clear counters, order the queries, run the persistent kernel
+  // capture: clear the counters, run the persistent kernel, merge
   cudaStream_t cs = b->capture_stream;
-  const size_t osmem = (size_t)dev::next_pow2(std::min(max_queries, kOrderCap)) * 8;
-  e = cudaFuncSetAttribute(order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem);
+  const size_t msmem = (size_t)dev::next_pow2(k) * 8 + (size_t)p.za_len * 4;
+  e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
   for (int gi = 0; gi < (b->can_dense ? 2 : 1) && e == cudaSuccess; ++gi) {
     b->dense = gi == 1;
     e = batch_dispatch(b, false);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       cudaMemsetAsync(b->counters, 0, b->counter_words * 4, cs);
-      order_kernel<<<1, 1024, osmem, cs>>>(b->desc);
       cudaError_t le = batch_dispatch(b, true);
+      merge_kernel<<<std::min<uint32_t>(max_queries, 152u * 16u), kMergeThreads, msmem, cs>>>(b->host_desc.merge);
       e = cudaStreamEndCapture(cs, &b->graph[gi]);
       if (e == cudaSuccess && le != cudaSuccess) e = le;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[gi], b->graph[gi], 0);
+    // the two kernel nodes: their arguments are set by each run
+    size_t n_nodes = 0;
+    if (e == cudaSuccess) e = cudaGraphGetNodes(b->graph[gi], nullptr, &n_nodes);
+    std::vector<cudaGraphNode_t> nodes(n_nodes);
+    if (e == cudaSuccess && n_nodes) e = cudaGraphGetNodes(b->graph[gi], nodes.data(), &n_nodes);
+    for (size_t i = 0; i < n_nodes && e == cudaSuccess; ++i) {
+      cudaGraphNodeType type;
+      e = cudaGraphNodeGetType(nodes[i], &type);
+      if (e != cudaSuccess || type != cudaGraphNodeTypeKernel) continue;
+      cudaKernelNodeParams kp;
+      e = cudaGraphKernelNodeGetParams(nodes[i], &kp);
+      if (e != cudaSuccess) break;
+      if (kp.func == reinterpret_cast<void*>(merge_kernel)) {
+        b->mnode[gi] = nodes[i];
+        b->mnode_params[gi] = kp;
+      } else {
+        b->node[gi] = nodes[i];
+        b->node_params[gi] = kp;
+      }
+    }
+    if (e == cudaSuccess && (!b->node[gi] || !b->mnode[gi])) e = cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) {
     free_batch(b);
@@ -364,12 +332,24 @@ extern "C" genie_status genie_batch_run(genie_batch* b, const genie_queries* que
   d.merge.ids = d_ids;
   d.merge.counts = d_counts;
   d.merge.n_valid = d_n_valid;
-  d.entries = queries->entries;
-  // pageable source: the runtime stages it before returning, so `d` may go
-  GENIE_CUDA_TRY(cudaMemcpyAsync(b->desc, &d, sizeof(d), cudaMemcpyHostToDevice, s));
   const bool dense = b->can_dense && queries->n_dense_entries > 0 &&
                      2 * queries->n_dense_entries >= queries->n_entries;
-  GENIE_CUDA_TRY(cudaGraphLaunch(b->exec[dense ? 1 : 0], s));
+  const int gi = dense ? 1 : 0;
+  // this batch's arguments on the two kernel nodes (copied by the calls; the
+  // graph's next launch uses them)
+  cudaKernelNodeParams kp = b->node_params[gi];
+  uint32_t* work = b->counters;
+  void* args[] = {&d.scan, &work};
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  GENIE_CUDA_TRY(cudaGraphExecKernelNodeSetParams(b->exec[gi], b->node[gi], &kp));
+  cudaKernelNodeParams mp = b->mnode_params[gi];
+  void* margs[] = {&d.merge};
+  mp.kernelParams = margs;
+  mp.extra = nullptr;
+  mp.gridDim = dim3(std::min<uint32_t>(queries->n_queries, 152u * 16u));
+  GENIE_CUDA_TRY(cudaGraphExecKernelNodeSetParams(b->exec[gi], b->mnode[gi], &mp));
+  GENIE_CUDA_TRY(cudaGraphLaunch(b->exec[gi], s));
   return GENIE_OK;
 }
 

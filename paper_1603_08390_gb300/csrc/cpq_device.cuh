@@ -324,9 +324,8 @@ __device__ __forceinline__ void slices_add8(uint32_t (&s)[8], const uint32_t* x)
 // Counts of objects 8q .. 8q+7 of a bitmap word from its slices, one byte
 // each (byte c = count of object 8q + c): the 8 x 8 bit matrix with row j =
 // byte q of slice j, transposed (three delta swaps).
-template <int Q>
-__device__ __forceinline__ unsigned long long slice_bytes(const uint32_t (&s)[8]) {
-  constexpr uint32_t sel = Q | ((Q + 4) << 4);
+__device__ __forceinline__ unsigned long long slice_bytes(const uint32_t (&s)[8], uint32_t q) {
+  const uint32_t sel = q | ((q + 4) << 4);
   const uint32_t lo = __byte_perm(__byte_perm(s[0], s[1], sel), __byte_perm(s[2], s[3], sel), 0x5410);
   const uint32_t hi = __byte_perm(__byte_perm(s[4], s[5], sel), __byte_perm(s[6], s[7], sel), 0x5410);
   unsigned long long x = ((unsigned long long)hi << 32) | lo, t;
@@ -339,60 +338,87 @@ __device__ __forceinline__ unsigned long long slice_bytes(const uint32_t (&s)[8]
   return x;
 }
 
-// Adds the counts of bitmap word w (local objects 32w .. 32w+31) to the
-// counter words that hold them (8-bit lanes: four objects per word; 16-bit:
-// two).  The calling thread owns those counter words.
+// 8 object counts (bytes, object c in byte c) as counter words: 8-bit lanes
+// (x, y of a uint2 as the words' values; z, w unused) or 16-bit lanes (a
+// uint4: objects 2i, 2i+1 in the low and high halves of word i).
 template <int LOG2W>
-__device__ __forceinline__ void slices_emit(uint32_t* bc, uint32_t w, const uint32_t (&s)[8]) {
-  if (!(s[0] | s[1] | s[2] | s[3] | s[4] | s[5] | s[6] | s[7])) return;
-  const unsigned long long c[4] = {slice_bytes<0>(s), slice_bytes<1>(s), slice_bytes<2>(s),
-                                   slice_bytes<3>(s)};
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const uint32_t lo = (uint32_t)c[q], hi = (uint32_t)(c[q] >> 32);
-    if (LOG2W == 3) {
-      bc[8 * w + 2 * q] += lo;
-      bc[8 * w + 2 * q + 1] += hi;
-    } else {  // 16-bit lanes: objects 2i, 2i+1 in the low and high halves
-      bc[16 * w + 4 * q] += __byte_perm(lo, 0u, 0x4140);
-      bc[16 * w + 4 * q + 1] += __byte_perm(lo, 0u, 0x4342);
-      bc[16 * w + 4 * q + 2] += __byte_perm(hi, 0u, 0x4140);
-      bc[16 * w + 4 * q + 3] += __byte_perm(hi, 0u, 0x4342);
-    }
+__device__ __forceinline__ uint4 lane_words(unsigned long long b) {
+  const uint32_t lo = (uint32_t)b, hi = (uint32_t)(b >> 32);
+  if (LOG2W == 3) return make_uint4(lo, hi, 0u, 0u);
+  return make_uint4(__byte_perm(lo, 0u, 0x4140), __byte_perm(lo, 0u, 0x4342),
+                    __byte_perm(hi, 0u, 0x4140), __byte_perm(hi, 0u, 0x4342));
+}
+
+// Adds the counter words of 8 objects to those at word index i: a uint2
+// (8-bit lanes) or uint4 (16-bit lanes) in shared memory.
+template <int LOG2W>
+__device__ __forceinline__ void lane_words_add(uint32_t* bc, uint32_t i, uint4 x) {
+  if (LOG2W == 3) {
+    uint2* p = reinterpret_cast<uint2*>(bc + i);
+    uint2 v = *p;
+    v.x += x.x;
+    v.y += x.y;
+    *p = v;
+  } else {
+    uint4* p = reinterpret_cast<uint4*>(bc + i);
+    uint4 v = *p;
+    v.x += x.x;
+    v.y += x.y;
+    v.z += x.z;
+    v.w += x.w;
+    *p = v;
   }
 }
 
-// What the dense phase needs of the search arguments (passed by value: a
-// reference to a kernel's parameters would copy them to local memory).
-struct DenseArgs {
-  const uint32_t* dense_slot;
-  const uint32_t* dense_bits;
-  const uint32_t* q_kw;
-  uint64_t map_words;
-  uint32_t block_shift;
-};
+// Adds the counts of bitmap word w (local objects 32w .. 32w+31) to the
+// counter words that hold them (8-bit lanes: four objects per word; 16-bit:
+// two).  The calling thread owns those words.  With
+// 16-bit lanes a word's four groups of 8 objects (16 bytes of counters each)
+// go in an order that starts at a group set by the thread's index, so that
+// the threads of a warp, which own words 128 bytes apart, spread their
+// accesses over the shared-memory banks.
+template <int LOG2W>
+__device__ __forceinline__ void slices_emit(uint32_t* bc, uint32_t w, const uint32_t (&s)[8]) {
+  if (!(s[0] | s[1] | s[2] | s[3] | s[4] | s[5] | s[6] | s[7])) return;
+  constexpr uint32_t WPG = 8u >> (5 - LOG2W);  // counter words per group of 8 objects
+#pragma unroll
+  for (uint32_t j = 0; j < 4; ++j) {
+    const uint32_t q = LOG2W == 4 ? (j + threadIdx.x) & 3u : j;
+    lane_words_add<LOG2W>(bc, (4 * w + q) * WPG, lane_words<LOG2W>(slice_bytes(s, q)));
+  }
+}
 
 // Adds the object bitmaps slots[0..n) (n <= 255) of range g to the Bitmap
-// Counter.  Each thread takes 32-object words in turn and reads sixteen
-// bitmaps' words at a time; all threads call it.
+// Counter.  Each thread takes two adjacent 32-object words at a time (one
+// 8-byte load per bitmap) and reads eight bitmaps per step; all threads call
+// it.
 template <int LOG2W>
-__device__ void dense_add(const DenseArgs& A, uint32_t g, uint32_t* bc, const uint32_t* slots,
+__device__ void dense_add(const ScanArgs& A, uint32_t g, uint32_t* bc, const uint32_t* slots,
                           uint32_t n) {
-  const uint32_t nwr = (1u << A.block_shift) >> 5;  // bitmap words of the range
-  const uint32_t* __restrict__ bits = A.dense_bits + (uint64_t)g * nwr;
-  const uint64_t mw = A.map_words;
-  for (uint32_t w = threadIdx.x; w < nwr; w += blockDim.x) {
-    uint32_t s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const uint32_t nwr = (1u << A.block_shift) >> 5;  // bitmap words of the range (even)
+  const uint2* __restrict__ bits = reinterpret_cast<const uint2*>(A.dense_bits + (uint64_t)g * nwr);
+  const uint64_t mw2 = A.map_words >> 1;  // map_words is a multiple of 8192
+  for (uint32_t p = threadIdx.x; p < (nwr >> 1); p += blockDim.x) {
+    uint32_t s0[8] = {0, 0, 0, 0, 0, 0, 0, 0}, s1[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint32_t d = 0;
-    for (; d + 16 <= n; d += 16) {
-      uint32_t x[16];
+    for (; d + 8 <= n; d += 8) {
+      uint32_t x0[8], x1[8];
 #pragma unroll
-      for (int e = 0; e < 16; ++e) x[e] = __ldg(bits + slots[d + e] * mw + w);
-      slices_add8(s, x);
-      slices_add8(s, x + 8);
+      for (int e = 0; e < 8; ++e) {
+        const uint2 v = __ldg(bits + slots[d + e] * mw2 + p);
+        x0[e] = v.x;
+        x1[e] = v.y;
+      }
+      slices_add8(s0, x0);
+      slices_add8(s1, x1);
     }
-    for (; d < n; ++d) slices_add1(s, __ldg(bits + slots[d] * mw + w));
-    slices_emit<LOG2W>(bc, w, s);
+    for (; d < n; ++d) {
+      const uint2 v = __ldg(bits + slots[d] * mw2 + p);
+      slices_add1(s0, v.x);
+      slices_add1(s1, v.y);
+    }
+    slices_emit<LOG2W>(bc, 2 * p, s0);
+    slices_emit<LOG2W>(bc, 2 * p + 1, s1);
   }
 }
 
@@ -615,7 +641,7 @@ struct BlockShared {
 // k) enter the hash table.  list: 2 * kKwBatch words of shared memory.
 // Returns the number of dense keywords added.  All threads call it.
 template <int LOG2W>
-__device__ __noinline__ uint32_t dense_phase(const DenseArgs A, uint32_t g, uint32_t qa, uint32_t qb,
+__device__ __noinline__ uint32_t dense_phase(const ScanArgs& A, uint32_t g, uint32_t qa, uint32_t qb,
                                              uint32_t* bc, uint32_t nwords, uint32_t* list,
                                              bool gated, BlockShared& S) {
   constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, MASK = (1u << W) - 1u;
@@ -766,9 +792,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   // dense keywords first: their bitmaps are added whole, their lists skipped
   // (the count stays in shared memory: the scan loop has no register to spare)
   if (DENSE && LOG2W >= 3) {
-    const uint32_t nd = dense_phase<LOG2W>(DenseArgs{A.dense_slot, A.dense_bits, A.q_kw,
-                                                     A.map_words, A.block_shift},
-                                           g, qa, qb, bc, nwords, reinterpret_cast<uint32_t*>(seg),
+    const uint32_t nd = dense_phase<LOG2W>(A, g, qa, qb, bc, nwords, reinterpret_cast<uint32_t*>(seg),
                                            !gateless, S);
     if (tid == 0) S.n_dense = nd;
   } else if (tid == 0) {
@@ -1027,7 +1051,7 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
 // 16-byte loads in flight per lane (a warp tile is 128 * U postings);
 // THREADS: the block size; DENSE: dense keywords are added as bitmaps.
 template <int LOG2W, int U, int THREADS, bool DENSE>
-__global__ void __launch_bounds__(THREADS, 1) scan_cpq_kernel(const ScanArgs A) {
+__global__ void __launch_bounds__(THREADS, 1) scan_cpq_kernel(const __grid_constant__ ScanArgs A) {
   extern __shared__ uint4 smem_raw[];
   __shared__ BlockShared S;
   cpq_item<LOG2W, U, DENSE>(A, blockIdx.x % A.n_sel, blockIdx.x / A.n_sel, smem_raw, S);

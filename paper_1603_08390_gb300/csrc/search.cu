@@ -109,7 +109,7 @@ cudaError_t run_pass(const genie_index* idx, const genie_queries* qs, uint32_t k
                      const genie_search_opts* o, unsigned long long* cand, uint32_t* at_hint,
                      uint32_t* hint_hist, uint32_t* ids, uint32_t* counts, uint32_t* n_valid,
                      cudaStream_t s) {
-  ScanArgs a;
+  ScanArgs a{};  // fields left unset are zero (NULL)
   a.kw_off = idx->kw_off;
   a.post_ids = idx->post_ids;
   a.chunk_pos = idx->chunk_pos;

@@ -97,3 +97,33 @@ def test_autotune_and_its_cache(tmp_path):
         assert len(f.read().strip().splitlines()) == 1
     batch = genie.Batch(idx, 48, qs.max_bound, 20, a)
     _check_oracle(_run_batch(batch, qs, 20), oracle.topk(w))
+
+
+def test_batch_dense_repeats_per_query_k_and_changing_batches():
+    """Zipf sets with object bitmaps (the dense graph): repeated keywords
+    count once per occurrence, per-query k, and batches of different sizes
+    replayed on one plan, against the oracle and the plain search."""
+    w = synth.sets(300_000, (16, 256), 1 << 16, 96, (8, 512), 10, config=33)
+    rng = np.random.default_rng(5)
+    # repeat a few keywords inside some queries (multisets)
+    q_kw, q_off = [], [0]
+    for q in range(w.n_queries):
+        kw = w.q_kw[w.q_off[q]:w.q_off[q + 1]]
+        if q % 3 == 0 and len(kw):
+            kw = np.concatenate([kw, kw[: rng.integers(1, min(len(kw), 4) + 1)]])
+        q_kw.append(kw)
+        q_off.append(q_off[-1] + len(kw))
+    w.q_kw = np.concatenate(q_kw).astype(np.uint32)
+    w.q_off = np.array(q_off, dtype=np.uint32)
+    w.k = rng.integers(1, 11, w.n_queries).astype(np.uint32)
+    idx = runner.build_index(w, dense_min_df=2000)
+    assert idx.info.dense_keywords > 0
+    batch = genie.Batch(idx, 96, 1024, 10)
+    parts = (w.subset(np.arange(0, 96)), w.subset(np.arange(0, 96, 2)), w.subset(np.arange(40, 41)))
+    for part in parts:
+        qs = runner.compile_queries(idx, part)
+        assert 2 * qs.n_dense_entries >= qs.n_entries  # the dense graph runs
+        d_k = runner.to_dev(np.asarray(part.k, dtype=np.uint32))
+        ref = oracle.topk(part)
+        _check_oracle(_run_batch(batch, qs, 10, d_k=d_k), ref)
+        _check_oracle(runner.search(idx, qs, part.k).host(), ref)
