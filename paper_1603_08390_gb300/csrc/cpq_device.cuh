@@ -727,6 +727,14 @@ __device__ __noinline__ uint32_t dense_phase(const ScanArgs& A, uint32_t g, uint
 // warp tile is 128 * U postings); DENSE: the range adds the bitmaps of the
 // query's dense keywords and scans only the other lists (a separate
 // instantiation, so that the plain scan's code is untouched by the dense one).
+// The tile loop's Gate mode, fixed per block (the loop is compiled once per
+// mode, so it holds no per-tile branch on it): 0 counting only (gateless), 1
+// the word-wide Gate test (lane headroom), 2 the per-lane Gate test.
+template <int M>
+struct GateMode {
+  static constexpr int value = M;
+};
+
 template <int LOG2W, int U, bool DENSE>
 __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_t g,
                                          uint4* smem_raw, BlockShared& S) {
@@ -877,94 +885,100 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
       start = locate(t, lo, hi);
       load(start, hi, v);
     }
-    while (t < total_tiles) {
-      // the tile after t: the next of this run, else the first of the warp's next run
-      const bool run_ends = t + 1 >= t_end;
-      if (run_ends) {
-        uint32_t r = 0;
-        if (lane == 0) r = atomicAdd(&S.next_run, 1u);
-        run = __shfl_sync(0xFFFFFFFFu, r, 0);
-      }
-      const uint32_t tn = run_ends ? run_first(run) : t + 1;
-      const uint32_t tn_end = run_ends ? run_last(run, tn) : t_end;
-      // Bitmap Counter: one sub-word atomic add per posting (the count update
-      // of Algorithm 1); val = the counter word before the add (0 for slots
-      // outside the list).  Every id of a sublist lies in this block's range.
-      uint32_t val[4 * kUnroll];
-      if (gateless) {  // counting only: no old value is needed
-        const uint32_t d0 = start + lane * 4 - lo, len = hi - lo;
-        const bool inside = start >= lo && start + kTile <= hi;
-#pragma unroll
-        for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
-          const uint32_t u = i >> 2, e = i & 3;
-          const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-          const uint32_t saddr = bc_adj + Lane<LOG2W>::byte_off(id);
-          if (inside) red_add_shared(saddr, Lane<LOG2W>::inc(id));
-          else red_add_shared_in(d0 + u * 128 + e, len, saddr, Lane<LOG2W>::inc(id));
+    auto tile_loop = [&](auto mode) {
+      constexpr int M = decltype(mode)::value;  // GateMode
+      while (t < total_tiles) {
+        // the tile after t: the next of this run, else the first of the warp's next run
+        const bool run_ends = t + 1 >= t_end;
+        if (run_ends) {
+          uint32_t r = 0;
+          if (lane == 0) r = atomicAdd(&S.next_run, 1u);
+          run = __shfl_sync(0xFFFFFFFFu, r, 0);
         }
-      } else if (start >= lo && start + kTile <= hi) {
+        const uint32_t tn = run_ends ? run_first(run) : t + 1;
+        const uint32_t tn_end = run_ends ? run_last(run, tn) : t_end;
+        // Bitmap Counter: one sub-word atomic add per posting (the count update
+        // of Algorithm 1); val = the counter word before the add (0 for slots
+        // outside the list).  Every id of a sublist lies in this block's range.
+        uint32_t val[4 * kUnroll];
+        if constexpr (M == 0) {  // counting only: no old value is needed
+          const uint32_t d0 = start + lane * 4 - lo, len = hi - lo;
+          const bool inside = start >= lo && start + kTile <= hi;
 #pragma unroll
-        for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
-          const uint32_t u = i >> 2, e = i & 3;
-          const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-          val[i] = atom_add_shared(bc_adj + Lane<LOG2W>::byte_off(id), Lane<LOG2W>::inc(id));
-        }
-      } else {  // a tile at either end of its list: slot positions checked one by one
-        const uint32_t d0 = start + lane * 4 - lo, len = hi - lo;
+          for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
+            const uint32_t u = i >> 2, e = i & 3;
+            const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
+            const uint32_t saddr = bc_adj + Lane<LOG2W>::byte_off(id);
+            if (inside) red_add_shared(saddr, Lane<LOG2W>::inc(id));
+            else red_add_shared_in(d0 + u * 128 + e, len, saddr, Lane<LOG2W>::inc(id));
+          }
+        } else if (start >= lo && start + kTile <= hi) {
 #pragma unroll
-        for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
-          const uint32_t u = i >> 2, e = i & 3;
-          const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-          val[i] = atom_add_shared_in(d0 + u * 128 + e, len, bc_adj + Lane<LOG2W>::byte_off(id),
-                                      Lane<LOG2W>::inc(id));
-        }
-      }
-      // Gate (Algorithm 1) for the postings whose new count reaches
-      // the (possibly stale) AuditThreshold: rare, so a tile is tested once.
-      // With headroom (every count below the lanes' top bit) the test runs
-      // on whole words: adding 2^(W-1) - (AT - 1) to every lane sets a lane's
-      // top bit exactly when the lane holds AT - 1 or more, without carries
-      // between lanes.  It also looks at the other lanes of each word: a
-      // false alarm costs only the exact test below.  Without headroom each
-      // posting's own lane is taken, before the ids are overwritten.
-      uint32_t at_c = 0;
-      bool hit = false;
-      if (!gateless && !swar) {
-        at_c = vld(&s_at);
-        uint32_t vmax = 0;
+          for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
+            const uint32_t u = i >> 2, e = i & 3;
+            const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
+            val[i] = atom_add_shared(bc_adj + Lane<LOG2W>::byte_off(id), Lane<LOG2W>::inc(id));
+          }
+        } else {  // a tile at either end of its list: slot positions checked one by one
+          const uint32_t d0 = start + lane * 4 - lo, len = hi - lo;
 #pragma unroll
-        for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
-          const uint32_t u = i >> 2, e = i & 3;
-          const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-          vmax = max(vmax, Lane<LOG2W>::pick(val[i], Lane<LOG2W>::sel(id)));
+          for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
+            const uint32_t u = i >> 2, e = i & 3;
+            const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
+            val[i] = atom_add_shared_in(d0 + u * 128 + e, len, bc_adj + Lane<LOG2W>::byte_off(id),
+                                        Lane<LOG2W>::inc(id));
+          }
         }
-        hit = vmax + 1 >= at_c;
-      }
-      const uint32_t c_lo = lo, c_hi = hi, c_start = start;
-      if (tn < total_tiles) {
-        if (!run_ends && start + kTile < hi) start += kTile;  // same segment
-        else start = locate(tn, lo, hi);
-        load(start, hi, v);
-      }
-      if (!gateless) {
-        if (swar) {
+        // Gate (Algorithm 1) for the postings whose new count reaches
+        // the (possibly stale) AuditThreshold: rare, so a tile is tested once.
+        // With headroom (every count below the lanes' top bit) the test runs
+        // on whole words: adding 2^(W-1) - (AT - 1) to every lane sets a lane's
+        // top bit exactly when the lane holds AT - 1 or more, without carries
+        // between lanes.  It also looks at the other lanes of each word: a
+        // false alarm costs only the exact test below.  Without headroom each
+        // posting's own lane is taken, before the ids are overwritten.
+        uint32_t at_c = 0;
+        bool hit = false;
+        if constexpr (M == 2) {
           at_c = vld(&s_at);
-          const uint32_t add = Lane<LOG2W>::kHigh - (at_c - 1) * Lane<LOG2W>::kOnes;
-          uint32_t acc = 0;
+          uint32_t vmax = 0;
 #pragma unroll
-          for (uint32_t i = 0; i < 4 * kUnroll; ++i) acc |= val[i] + add;
-          hit = (acc & Lane<LOG2W>::kHigh) != 0;
+          for (uint32_t i = 0; i < 4 * kUnroll; ++i) {
+            const uint32_t u = i >> 2, e = i & 3;
+            const uint32_t id = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
+            vmax = max(vmax, Lane<LOG2W>::pick(val[i], Lane<LOG2W>::sel(id)));
+          }
+          hit = vmax + 1 >= at_c;
         }
-        if (__any_sync(0xFFFFFFFFu, hit)) {
-          TileWords<U> tw;
+        const uint32_t c_lo = lo, c_hi = hi, c_start = start;
+        if (tn < total_tiles) {
+          if (!run_ends && start + kTile < hi) start += kTile;  // same segment
+          else start = locate(tn, lo, hi);
+          load(start, hi, v);
+        }
+        if constexpr (M != 0) {
+          if constexpr (M == 1) {
+            at_c = vld(&s_at);
+            const uint32_t add = Lane<LOG2W>::kHigh - (at_c - 1) * Lane<LOG2W>::kOnes;
+            uint32_t acc = 0;
 #pragma unroll
-          for (uint32_t i = 0; i < 4 * kUnroll; ++i) tw.w[i] = val[i];
-          gate_tile<LOG2W, U>(S.gate, post_ids, c_start, c_lo, c_hi, tw, at_c);
+            for (uint32_t i = 0; i < 4 * kUnroll; ++i) acc |= val[i] + add;
+            hit = (acc & Lane<LOG2W>::kHigh) != 0;
+          }
+          if (__any_sync(0xFFFFFFFFu, hit)) {
+            TileWords<U> tw;
+#pragma unroll
+            for (uint32_t i = 0; i < 4 * kUnroll; ++i) tw.w[i] = val[i];
+            gate_tile<LOG2W, U>(S.gate, post_ids, c_start, c_lo, c_hi, tw, at_c);
+          }
         }
+        t = tn;
+        t_end = tn_end;
       }
-      t = tn;
-      t_end = tn_end;
-    }
+    };
+    if (gateless) tile_loop(GateMode<0>{});
+    else if (swar) tile_loop(GateMode<1>{});
+    else tile_loop(GateMode<2>{});
     __syncthreads();
   }
 
