@@ -148,23 +148,30 @@ namespace {
 
 // Stable scatter of one tile by the digit at `shift`.  A pair's destination
 // is tile_off[d * n_tiles + tile] (the pairs of digit d in earlier tiles and
-// of smaller digits everywhere, from the scan of the histograms) plus the
-// pairs of digit d before it in the tile.  Warp w ranks the tile's pairs
+// of smaller digits everywhere, from the scan of the histograms) plus its
+// rank among the tile's pairs of digit d.  Warp w ranks the tile's pairs
 // [512 w, 512 w + 512) in 16 rounds of 32 consecutive pairs: the lanes that
 // share a digit in a round find each other with match.any, take their order
 // from their lane numbers and their base from the warp's running count of the
-// digit; the counts of the warps before it are added afterwards.
-__global__ void radix_scatter_kernel(const uint32_t* __restrict__ keys,
-                                     const uint32_t* __restrict__ vals, uint32_t n, uint32_t shift,
-                                     uint32_t nd, uint32_t n_tiles,
-                                     const uint32_t* __restrict__ tile_off,
-                                     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
+// digit; the counts of the warps before it are added afterwards.  The tile is
+// then laid out in shared memory in destination order and written from
+// there, so that consecutive threads write consecutive addresses.
+__global__ void __launch_bounds__(kRadixThreads)
+    radix_scatter_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                         uint32_t n, uint32_t shift, uint32_t nd, uint32_t n_tiles,
+                         const uint32_t* __restrict__ tile_off, uint32_t* __restrict__ keys_out,
+                         uint32_t* __restrict__ vals_out) {
   __shared__ uint32_t wh[kRadixWarps][kDigits];
+  __shared__ uint32_t loc[kDigits];   // first tile position of each digit
+  __shared__ uint32_t glob[kDigits];  // first destination of each digit's pairs of the tile
+  __shared__ uint32_t sk[kRadixTile], sv[kRadixTile];
+  __shared__ uint32_t scratch[33];
   const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 #pragma unroll
   for (uint32_t w = 0; w < kRadixWarps; ++w) wh[w][tid] = 0;
   __syncthreads();
-  const uint64_t wbase = (uint64_t)blockIdx.x * kRadixTile + warp * (32u * kRadixItems);
+  const uint64_t tile_start = (uint64_t)blockIdx.x * kRadixTile;
+  const uint64_t wbase = tile_start + warp * (32u * kRadixItems);
   const uint32_t lt = (1u << lane) - 1u;
   uint32_t k[kRadixItems], v[kRadixItems], r[kRadixItems];
 #pragma unroll
@@ -185,24 +192,36 @@ __global__ void radix_scatter_kernel(const uint32_t* __restrict__ keys,
     __syncwarp();
   }
   __syncthreads();
-  // thread d: pairs of digit d in the warps before each warp, plus the base
-  if (tid < nd) {
-    uint32_t run = tile_off[(uint64_t)tid * n_tiles + blockIdx.x];
+  // thread d: the tile's pairs of digit d in the warps before each warp
+  uint32_t cnt = 0;
 #pragma unroll
-    for (uint32_t w = 0; w < kRadixWarps; ++w) {
-      const uint32_t c = wh[w][tid];
-      wh[w][tid] = run;
-      run += c;
-    }
+  for (uint32_t w = 0; w < kRadixWarps; ++w) {
+    const uint32_t c = wh[w][tid];
+    wh[w][tid] = cnt;
+    cnt += c;
   }
+  uint32_t tot;
+  const uint32_t first = dev::block_exclusive_scan(cnt, scratch, &tot);
+  loc[tid] = first;
+  glob[tid] = tid < nd ? tile_off[(uint64_t)tid * n_tiles + blockIdx.x] : 0u;
   __syncthreads();
 #pragma unroll
   for (uint32_t j = 0; j < kRadixItems; ++j) {
     if (wbase + j * 32 + lane < n) {
-      const uint32_t dst = wh[warp][(k[j] >> shift) & (kDigits - 1)] + r[j];
-      keys_out[dst] = k[j];
-      vals_out[dst] = v[j];
+      const uint32_t d = (k[j] >> shift) & (kDigits - 1);
+      const uint32_t pos = loc[d] + wh[warp][d] + r[j];
+      sk[pos] = k[j];
+      sv[pos] = v[j];
     }
+  }
+  __syncthreads();
+  const uint32_t tile_n = (uint32_t)min((uint64_t)kRadixTile, (uint64_t)n - tile_start);
+  for (uint32_t i = tid; i < tile_n; i += kRadixThreads) {
+    const uint32_t kk = sk[i];
+    const uint32_t d = (kk >> shift) & (kDigits - 1);
+    const uint32_t dst = glob[d] + (i - loc[d]);
+    keys_out[dst] = kk;
+    vals_out[dst] = sv[i];
   }
 }
 
