@@ -230,8 +230,9 @@ typedef struct {
   /* Tuning (0 = automatic): log2 of object ids counted by one block, threads
    * per block (512, 768, 896 or 1024), hash-table slots per block (power of
    * two >= 32), 16-byte loads in flight per thread (2 or 4 with 768 or 1024
-   * threads, 2 with 896, 4 or 8 with 512).  genie_search_shape reports what
-   * the automatic choice is. */
+   * threads, 2 with 896, 2, 4 or 8 with 512; 512 threads with 2 run two
+   * blocks per SM where two blocks' shared memory fits an SM).
+   * genie_search_shape reports what the automatic choice is. */
   uint32_t block_shift;
   uint32_t threads;
   uint32_t ht_slots;
@@ -340,7 +341,9 @@ genie_status genie_search_host(const genie_index* index, const uint32_t* h_q_off
  * synchronisation.  Automatic choices: counters wide enough for the largest
  * count bound; 128 KB of counters per block; 512 threads with eight loads per
  * lane when a block's mean sublist per keyword holds at least 4096 postings,
- * else 1024 threads with two (768 with 4-bit counters).  Errors: INVALID_ARG
+ * else 1024 threads with two (768 with 4-bit counters); a search that adds
+ * object bitmaps with 8-bit counters runs two 512-thread blocks per SM with
+ * two loads per lane, each over 64 KB of counters.  Errors: INVALID_ARG
  * (NULL handles, k, handles from another index, tuning values out of range).
  */
 genie_status genie_search_shape(const genie_index* index, const genie_queries* queries, uint32_t k,

@@ -170,6 +170,8 @@ extern "C" genie_status genie_batch_create(const genie_index* index, uint32_t ma
   Plan p;
   genie_status st = make_plan(index, &probe, k, &so, &p);
   if (st != GENIE_OK) return st;
+  if (p.threads == 512 && p.unroll == 2)
+    return fail(GENIE_ERR_INVALID_ARG, "genie_batch_create: 512 threads run 4 or 8 loads per lane in a batch");
   genie_batch* b = new (std::nothrow) genie_batch();
   if (!b) return fail(GENIE_ERR_OUT_OF_MEMORY, "genie_batch_create: host allocation");
   cudaGetDevice(&b->device);

@@ -89,6 +89,7 @@ cudaError_t launch_scan(const ScanArgs& a, const Plan& p, cudaStream_t s) {
 template <int LOG2W>
 cudaError_t dispatch_width(const ScanArgs& a, const Plan& p, cudaStream_t s) {
   if (p.threads == 512) return p.unroll == 8 ? launch_scan<LOG2W, 8, 512>(a, p, s)
+                             : p.unroll == 2 ? launch_scan<LOG2W, 2, 512>(a, p, s)
                                              : launch_scan<LOG2W, 4, 512>(a, p, s);
   if (p.threads == 768) return p.unroll == 4 ? launch_scan<LOG2W, 4, 768>(a, p, s)
                                              : launch_scan<LOG2W, 2, 768>(a, p, s);

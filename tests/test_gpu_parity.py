@@ -154,11 +154,22 @@ def test_search_shape_reports_the_automatic_choice():
     qs = runner.compile_queries(idx, w)
     sh = genie.genie_search_shape(idx, qs, 10)
     assert (sh.counter_bits, sh.threads, sh.unroll, sh.dense) == (8, 512, 8, 0)
-    # the same lists as bitmaps: nothing long is left to scan, so the short shape
+    # the same lists as bitmaps: nothing long is left to scan, so the short
+    # shape (one object range: it cannot be halved)
     idx = runner.build_index(w)
     qs = runner.compile_queries(idx, w)
     sh = genie.genie_search_shape(idx, qs, 10)
     assert (sh.counter_bits, sh.threads, sh.unroll, sh.dense) == (8, 1024, 2, 1)
+    assert_same(runner.search(idx, qs, 10).host(), oracle.topk(w))
+    # bitmaps with 8-bit counters over several ranges: two 512-thread blocks
+    # per SM with two loads per lane, each over half the usual object range
+    w = synth.sets(300_000, (16, 64), 1 << 12, 24, (8, 100), 10, config=202)
+    idx = runner.build_index(w)
+    qs = runner.compile_queries(idx, w)
+    sh = genie.genie_search_shape(idx, qs, 10)
+    assert (sh.counter_bits, sh.threads, sh.unroll, sh.dense) == (8, 512, 2, 1)
+    assert sh.block_shift == 16 and sh.n_groups == 5
+    assert_same(runner.search(idx, qs, 10).host(), oracle.topk(w))
     assert_same(runner.search(idx, qs, 10).host(), oracle.topk(w))
     # 4-bit counters keep 768 threads for short sublists (3 items of 5 values: B = 15)
     w = synth.relational(n_objects=70_001, n_queries=8, config=11, items_per_query=3)
