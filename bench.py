@@ -682,11 +682,13 @@ def leg_batched(args):
 
     k = 10
     w = synth.config(3)
+    if args.queries:  # a smaller batch of the same queries (profiling captures)
+        w = w.subset(np.arange(0, w.n_queries, max(1, w.n_queries // args.queries))[:args.queries])
     idx = runner.build_index(w)
     Q = w.n_queries
     d_q_off, d_q_kw = runner.to_dev(w.q_off), runner.to_dev(w.q_kw)
     stream = torch.cuda.current_stream()
-    sample = w.subset(np.arange(0, Q, Q // 512)[:512])
+    sample = w.subset(np.arange(0, Q, max(1, Q // 512))[:512])
     sq = runner.compile_queries(idx, sample)
     t0 = time.perf_counter()
     tuned = genie.genie_autotune(idx, sq, k, os.path.join(tempfile.gettempdir(), "genie_tune.txt"))

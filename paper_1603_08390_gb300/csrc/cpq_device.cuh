@@ -665,14 +665,26 @@ __device__ __noinline__ uint32_t dense_phase(const ScanArgs& A, uint32_t g, uint
   GateCtx& G = S.gate;
   uint32_t* za = G.g.za;
   const uint32_t at0 = S.at, B = G.B;
-  // ZA[c] = #objects with count c (c >= at0) ...
+  // ZA[c] = #objects with count c (c >= at0) ...  With lane headroom a word's
+  // lanes are looked at only when the word-wide test (as in the Gate: adding
+  // 2^(W-1) - at0 to every lane sets a lane's top bit exactly when the lane
+  // holds at0 or more) says one of them reaches at0.  The objects found are
+  // also listed (up to `cap`; the dense slots are added, so `list` is free)
+  // for the hash-table pass below.
+  const bool headroom = B < (1u << (W - 1));
+  const uint32_t add = Lane<LOG2W>::kHigh - at0 * Lane<LOG2W>::kOnes;
+  if (tid == 0) S.n = 0;
+  __syncthreads();
   for (uint32_t w = tid; w < nwords; w += blockDim.x) {
     const uint32_t word = bc[w];
-    if (word) {
+    if (headroom ? !((word + add) & Lane<LOG2W>::kHigh) : !word) continue;
 #pragma unroll
-      for (uint32_t l = 0; l < PER; ++l) {
-        const uint32_t c = (word >> (l * W)) & MASK;
-        if (c >= at0 && c <= B) atomicAdd(&za[c], 1u);
+    for (uint32_t l = 0; l < PER; ++l) {
+      const uint32_t c = (word >> (l * W)) & MASK;
+      if (c >= at0 && c <= B) {
+        atomicAdd(&za[c], 1u);
+        const uint32_t i = atomicAdd(&S.n, 1u);
+        if (i < cap) list[i] = w * PER + l;
       }
     }
   }
@@ -699,8 +711,16 @@ __device__ __noinline__ uint32_t dense_phase(const ScanArgs& A, uint32_t g, uint
     S.at = a;
   }
   __syncthreads();
-  const uint32_t a = S.at;
-  if (a <= B && za[a] > 0) {  // fewer than k objects: presence bits and hash-table entries
+  const uint32_t a = S.at, n_found = S.n;
+  if (a <= B && za[a] > 0 && n_found <= cap) {  // the listed objects at or above a
+    for (uint32_t i = tid; i < n_found; i += blockDim.x) {
+      const uint32_t local = list[i];
+      if (lane_count<LOG2W>(bc, local) >= a) {
+        atomicOr(&G.g.present[local >> 5], 1u << (local & 31));
+        ht_insert<LOG2W>(G.g, G.obj_base + local, G.obj_base, G.ht_mask, G.ht_bits);
+      }
+    }
+  } else if (a <= B && za[a] > 0) {  // fewer than k objects: presence bits and hash-table entries
     for (uint32_t w = tid; w < nwords; w += blockDim.x) {
       const uint32_t word = bc[w];
       if (word) {

@@ -118,7 +118,7 @@ def test_gate_test_on_both_sides_of_lane_headroom(vocab, obj_len, b):
 # Every launch shape the library compiles (threads x 16-byte loads per lane),
 # on both sides of the lane-headroom limit, with ragged sublists and per-query k.
 @pytest.mark.parametrize("threads,unroll", [(768, 2), (768, 4), (896, 2), (1024, 2), (1024, 4),
-                                            (512, 4), (512, 8)])
+                                            (512, 2), (512, 4), (512, 8)])
 @pytest.mark.parametrize("b", [127, 200])
 def test_every_launch_shape(threads, unroll, b):
     w = synth.sets(70_001, (60, 240), 260, 24, (b, b), 10, config=300 + b)
