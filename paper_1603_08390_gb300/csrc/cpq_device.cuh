@@ -63,6 +63,8 @@ struct ScanArgs {
 constexpr uint32_t kMaxProbe = 32;   // hash-table probes before an insert gives up
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kTilePrePad = 36;  // tile prefix sums: sentinels read by a warp-wide step
+// the tile prefix sums' room holds 255 bitmap pointers (8-byte aligned) in the dense phase
+static_assert((kKwBatch + kTilePrePad) * 4 >= 255 * 8 + 4, "room for the dense pointers");
 constexpr uint32_t kRun = 8;         // consecutive tiles a warp claims as one run
 
 size_t scan_smem_bytes(uint32_t log2w, uint32_t block_shift, uint32_t ht_slots, uint32_t za_len,
@@ -388,16 +390,15 @@ __device__ __forceinline__ void slices_emit(uint32_t* bc, uint32_t w, const uint
   }
 }
 
-// Adds the object bitmaps slots[0..n) (n <= 255) of range g to the Bitmap
-// Counter.  Each thread takes two adjacent 32-object words at a time (one
+// Adds n <= 255 object bitmaps to the Bitmap Counter of range g: ptrs[i] =
+// the range's slice of bitmap i, as 8-byte words (in shared memory, set once
+// per block).  Each thread takes two adjacent 32-object words at a time (one
 // 8-byte load per bitmap) and reads eight bitmaps per step; all threads call
 // it.
 template <int LOG2W>
-__device__ void dense_add(const ScanArgs& A, uint32_t g, uint32_t* bc, const uint32_t* slots,
+__device__ void dense_add(const ScanArgs& A, uint32_t g, uint32_t* bc, const uint2* const* ptrs,
                           uint32_t n) {
   const uint32_t nwr = (1u << A.block_shift) >> 5;  // bitmap words of the range (even)
-  const uint2* __restrict__ bits = reinterpret_cast<const uint2*>(A.dense_bits + (uint64_t)g * nwr);
-  const uint64_t mw2 = A.map_words >> 1;  // map_words is a multiple of 8192
   for (uint32_t p = threadIdx.x; p < (nwr >> 1); p += blockDim.x) {
     uint32_t s0[8] = {0, 0, 0, 0, 0, 0, 0, 0}, s1[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint32_t d = 0;
@@ -405,7 +406,7 @@ __device__ void dense_add(const ScanArgs& A, uint32_t g, uint32_t* bc, const uin
       uint32_t x0[8], x1[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        const uint2 v = __ldg(bits + slots[d + e] * mw2 + p);
+        const uint2 v = __ldg(ptrs[d + e] + p);
         x0[e] = v.x;
         x1[e] = v.y;
       }
@@ -413,7 +414,7 @@ __device__ void dense_add(const ScanArgs& A, uint32_t g, uint32_t* bc, const uin
       slices_add8(s1, x1);
     }
     for (; d < n; ++d) {
-      const uint2 v = __ldg(bits + slots[d] * mw2 + p);
+      const uint2 v = __ldg(ptrs[d] + p);
       slices_add1(s0, v.x);
       slices_add1(s1, v.y);
     }
@@ -638,12 +639,13 @@ struct BlockShared {
 // Gate would hold after these counts -- ZA[i] = #objects with count >= i for
 // i >= AT (each object passes every level up to its count) -- AT advances
 // past the full levels, and the objects at or above the new AT (fewer than
-// k) enter the hash table.  list: 2 * kKwBatch words of shared memory.
+// k) enter the hash table.  list: 2 * kKwBatch words of shared memory; ptrs:
+// room for 255 pointers, 8-byte aligned, in shared memory.
 // Returns the number of dense keywords added.  All threads call it.
 template <int LOG2W>
 __device__ __noinline__ uint32_t dense_phase(const ScanArgs& A, uint32_t g, uint32_t qa, uint32_t qb,
                                              uint32_t* bc, uint32_t nwords, uint32_t* list,
-                                             bool gated, BlockShared& S) {
+                                             const uint2** ptrs, bool gated, BlockShared& S) {
   constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, MASK = (1u << W) - 1u;
   const uint32_t tid = threadIdx.x, cap = 2 * kKwBatch;
   uint32_t total = 0;
@@ -657,7 +659,16 @@ __device__ __noinline__ uint32_t dense_phase(const ScanArgs& A, uint32_t g, uint
     }
     __syncthreads();
     const uint32_t nd = S.n;
-    for (uint32_t d0 = 0; d0 < nd; d0 += 255) dense_add<LOG2W>(A, g, bc, list + d0, min(255u, nd - d0));
+    const uint32_t nwr = (1u << A.block_shift) >> 5;
+    const uint2* base = reinterpret_cast<const uint2*>(A.dense_bits + (uint64_t)g * nwr);
+    for (uint32_t d0 = 0; d0 < nd; d0 += 255) {
+      const uint32_t m = min(255u, nd - d0);
+      __syncthreads();  // the pointers of the previous group are read
+      for (uint32_t i = threadIdx.x; i < m; i += blockDim.x)
+        ptrs[i] = base + list[d0 + i] * (A.map_words >> 1);
+      __syncthreads();
+      dense_add<LOG2W>(A, g, bc, ptrs, m);
+    }
     total += nd;
     __syncthreads();  // the list is refilled, the counters are read next
   }
@@ -820,8 +831,11 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   // dense keywords first: their bitmaps are added whole, their lists skipped
   // (the count stays in shared memory: the scan loop has no register to spare)
   if (DENSE && LOG2W >= 3) {
+    // the tile prefix sums are not in use yet: room for the bitmap pointers
+    const uint2** ptrs = reinterpret_cast<const uint2**>(
+        (reinterpret_cast<uintptr_t>(tile_pre) + 7) & ~(uintptr_t)7);
     const uint32_t nd = dense_phase<LOG2W>(A, g, qa, qb, bc, nwords, reinterpret_cast<uint32_t*>(seg),
-                                           !gateless, S);
+                                           ptrs, !gateless, S);
     if (tid == 0) S.n_dense = nd;
   } else if (tid == 0) {
     S.n_dense = 0;
