@@ -628,6 +628,7 @@ struct BlockShared {
   uint32_t tie_floor; // ties below it are left out of the read-out
   uint32_t next_run;  // next run of tiles to be claimed
   uint32_t n_dense;   // dense keywords whose bitmaps the range added
+  uint32_t n_found;   // objects the dense phase found at or above AT
   GateCtx gate;       // the Gate's pointers and query constants
   uint32_t scratch[33];
   unsigned long long scratch64[33];
@@ -649,24 +650,33 @@ __device__ __noinline__ uint32_t dense_phase(const ScanArgs& A, uint32_t g, uint
   constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, MASK = (1u << W) - 1u;
   const uint32_t tid = threadIdx.x, cap = 2 * kKwBatch;
   uint32_t total = 0;
+  const uint32_t nwr = (1u << A.block_shift) >> 5;
+  const uint2* base = reinterpret_cast<const uint2*>(A.dense_bits + (uint64_t)g * nwr);
+  const uint64_t mw2 = A.map_words >> 1;
   for (uint32_t kb = qa; kb < qb; kb += cap) {
     const uint32_t nk = min(cap, qb - kb);
-    if (tid == 0) S.n = 0;
-    __syncthreads();
+    if (kb != qa) {  // S.n starts at 0 (the reset of the work item)
+      if (tid == 0) S.n = 0;
+      __syncthreads();
+    }
+    // the list of slots, and the pointers of its first 255 bitmaps
     for (uint32_t i = tid; i < nk; i += blockDim.x) {
       const uint32_t sl = A.dense_slot[A.q_kw[kb + i]];
-      if (sl != kNoDense) list[atomicAdd(&S.n, 1u)] = sl;
+      if (sl != kNoDense) {
+        const uint32_t j = atomicAdd(&S.n, 1u);
+        list[j] = sl;
+        if (j < 255) ptrs[j] = base + sl * mw2;
+      }
     }
     __syncthreads();
     const uint32_t nd = S.n;
-    const uint32_t nwr = (1u << A.block_shift) >> 5;
-    const uint2* base = reinterpret_cast<const uint2*>(A.dense_bits + (uint64_t)g * nwr);
     for (uint32_t d0 = 0; d0 < nd; d0 += 255) {
       const uint32_t m = min(255u, nd - d0);
-      __syncthreads();  // the pointers of the previous group are read
-      for (uint32_t i = threadIdx.x; i < m; i += blockDim.x)
-        ptrs[i] = base + list[d0 + i] * (A.map_words >> 1);
-      __syncthreads();
+      if (d0) {  // the next group's pointers, once the last group's are read
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) ptrs[i] = base + list[d0 + i] * mw2;
+        __syncthreads();
+      }
       dense_add<LOG2W>(A, g, bc, ptrs, m);
     }
     total += nd;
@@ -684,8 +694,6 @@ __device__ __noinline__ uint32_t dense_phase(const ScanArgs& A, uint32_t g, uint
   // for the hash-table pass below.
   const bool headroom = B < (1u << (W - 1));
   const uint32_t add = Lane<LOG2W>::kHigh - at0 * Lane<LOG2W>::kOnes;
-  if (tid == 0) S.n = 0;
-  __syncthreads();
   for (uint32_t w = tid; w < nwords; w += blockDim.x) {
     const uint32_t word = bc[w];
     if (headroom ? !((word + add) & Lane<LOG2W>::kHigh) : !word) continue;
@@ -694,7 +702,7 @@ __device__ __noinline__ uint32_t dense_phase(const ScanArgs& A, uint32_t g, uint
       const uint32_t c = (word >> (l * W)) & MASK;
       if (c >= at0 && c <= B) {
         atomicAdd(&za[c], 1u);
-        const uint32_t i = atomicAdd(&S.n, 1u);
+        const uint32_t i = atomicAdd(&S.n_found, 1u);  // zero since the reset
         if (i < cap) list[i] = w * PER + l;
       }
     }
@@ -722,7 +730,7 @@ __device__ __noinline__ uint32_t dense_phase(const ScanArgs& A, uint32_t g, uint
     S.at = a;
   }
   __syncthreads();
-  const uint32_t a = S.at, n_found = S.n;
+  const uint32_t a = S.at, n_found = S.n_found;
   if (a <= B && za[a] > 0 && n_found <= cap) {  // the listed objects at or above a
     for (uint32_t i = tid; i < n_found; i += blockDim.x) {
       const uint32_t local = list[i];
@@ -819,6 +827,8 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
       S.gateless = A.no_gate || (A.at_hint && s_at == 1);
       s_flags[0] = 0;
       s_flags[1] = 0;
+      s_n = 0;  // the dense phase's counters
+      S.n_found = 0;
       S.gate = GateCtx{GateState{za, present, ht, bc, &s_at, s_flags}, kq, B, obj_base, ht_mask,
                        ht_bits, 0u, 0u};
     }
