@@ -801,6 +801,18 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   const uint32_t nwarps = blockDim.x >> 5;
   const uint32_t q = A.q_sel ? A.q_sel[qi] : qi;
   const uint32_t c0 = g * A.chunks_per_block, c1 = min(c0 + A.chunks_per_block, A.n_chunks);
+  const uint32_t qa = A.q_off[q], qb = A.q_off[q + 1];
+  // The first keyword batch's sublist bounds, loaded before the reset so that
+  // their chain of loads overlaps it (not in the dense instantiation, whose
+  // bitmap phase comes in between).
+  uint32_t pre_lo = 0, pre_hi = 0;
+  if (!DENSE && tid < min(kKwBatch, qb - qa)) {
+    const uint32_t kw = A.q_kw[qa + tid];
+    const uint64_t base = A.kw_off[kw];
+    const uint32_t* row = A.chunk_pos + (uint64_t)kw * (A.n_chunks + 1);
+    pre_lo = (uint32_t)(base + row[c0]);
+    pre_hi = (uint32_t)(base + row[c1]);
+  }
 
   // ---- reset this block's c-PQ ------------------------------------------
   // The query's k and bound and the range's first id live in S.gate from
@@ -837,7 +849,6 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   const bool gateless = S.gateless;
   // every count of the range stays below the top bit of its lane
   const bool swar = S.gate.B < (1u << ((1u << LOG2W) - 1));
-  const uint32_t qa = A.q_off[q], qb = A.q_off[q + 1];
   // dense keywords first: their bitmaps are added whole, their lists skipped
   // (the count stays in shared memory: the scan loop has no register to spare)
   if (DENSE && LOG2W >= 3) {
@@ -863,13 +874,16 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     const uint32_t nk = min(kKwBatch, qb - kb);
     uint32_t ntiles = 0;
     if (tid < nk) {
-      const uint32_t kw = A.q_kw[kb + tid];
-      uint32_t lo = 0, hi = 0;
-      if (!DENSE || LOG2W < 3 || A.dense_slot[kw] == kNoDense) {  // a dense keyword's list is skipped
-        const uint64_t base = A.kw_off[kw];
-        const uint32_t* row = A.chunk_pos + (uint64_t)kw * stride;
-        lo = (uint32_t)(base + row[c0]);
-        hi = (uint32_t)(base + row[c1]);
+      uint32_t lo = pre_lo, hi = pre_hi;
+      if (DENSE || kb != qa) {
+        const uint32_t kw = A.q_kw[kb + tid];
+        lo = hi = 0;
+        if (!DENSE || LOG2W < 3 || A.dense_slot[kw] == kNoDense) {  // a dense keyword's list is skipped
+          const uint64_t base = A.kw_off[kw];
+          const uint32_t* row = A.chunk_pos + (uint64_t)kw * stride;
+          lo = (uint32_t)(base + row[c0]);
+          hi = (uint32_t)(base + row[c1]);
+        }
       }
       seg[tid] = make_uint2(lo, hi);
       ntiles = hi > lo ? (hi - (lo & ~3u) + kTile - 1) / kTile : 0;
