@@ -822,14 +822,20 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     const uint32_t B = A.bound[q];
     const uint32_t obj_base = g << A.block_shift;
     const uint32_t ht_mask = A.ht_slots - 1, ht_bits = 31 - __clz(A.ht_slots);
+    // the seed's loads go out before the zeroing and are used after it (a
+    // hint read a little early is still a valid seed: hints only grow)
+    uint32_t seed0 = 1u, hint0 = 0u;
+    if (tid == 0) {
+      if (A.seed) seed0 = A.seed[q];
+      if (A.at_hint) hint0 = vld(&A.at_hint[qi]);
+    }
     uint4* b4 = reinterpret_cast<uint4*>(bc);
     const uint4 z4 = make_uint4(0, 0, 0, 0);
     for (uint32_t i = tid; i < ((nwords + npresent) >> 2); i += blockDim.x) b4[i] = z4;
     for (uint32_t i = tid; i < A.ht_slots; i += blockDim.x) ht[i] = kEmpty;
     for (uint32_t i = tid; i < B + 2; i += blockDim.x) za[i] = 0;
     if (tid == 0) {
-      uint32_t s0 = A.seed ? A.seed[q] : 1u;
-      if (A.at_hint) s0 = max(s0, vld(&A.at_hint[qi]));
+      const uint32_t s0 = max(seed0, hint0);
       s_at = max(1u, min(s0, B + 1));
       S.at0 = s_at;
       // A range that starts before any range of its query has finished (no
