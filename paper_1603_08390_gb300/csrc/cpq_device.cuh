@@ -640,12 +640,15 @@ struct BlockShared {
 // Gate would hold after these counts -- ZA[i] = #objects with count >= i for
 // i >= AT (each object passes every level up to its count) -- AT advances
 // past the full levels, and the objects at or above the new AT (fewer than
-// k) enter the hash table.  list: 2 * kKwBatch words of shared memory; ptrs:
+// k) enter the hash table.  pre_slot: dense_slot of keyword qa + threadIdx.x
+// (loaded by the caller; kNoDense past qb).  list: 2 * kKwBatch words of
+// shared memory; ptrs:
 // room for 255 pointers, 8-byte aligned, in shared memory.
 // Returns the number of dense keywords added.  All threads call it.
 template <int LOG2W>
 __device__ __noinline__ uint32_t dense_phase(const ScanArgs& A, uint32_t g, uint32_t qa, uint32_t qb,
-                                             uint32_t* bc, uint32_t nwords, uint32_t* list,
+                                             uint32_t pre_slot, uint32_t* bc, uint32_t nwords,
+                                             uint32_t* list,
                                              const uint2** ptrs, bool gated, BlockShared& S) {
   constexpr uint32_t W = 1u << LOG2W, PER = 32u / W, MASK = (1u << W) - 1u;
   const uint32_t tid = threadIdx.x, cap = 2 * kKwBatch;
@@ -661,7 +664,7 @@ __device__ __noinline__ uint32_t dense_phase(const ScanArgs& A, uint32_t g, uint
     }
     // the list of slots, and the pointers of its first 255 bitmaps
     for (uint32_t i = tid; i < nk; i += blockDim.x) {
-      const uint32_t sl = A.dense_slot[A.q_kw[kb + i]];
+      const uint32_t sl = (kb == qa && i == tid) ? pre_slot : A.dense_slot[A.q_kw[kb + i]];
       if (sl != kNoDense) {
         const uint32_t j = atomicAdd(&S.n, 1u);
         list[j] = sl;
@@ -813,6 +816,10 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     pre_lo = (uint32_t)(base + row[c0]);
     pre_hi = (uint32_t)(base + row[c1]);
   }
+  // In the dense instantiation, the bitmap slot of the thread's first keyword
+  uint32_t pre_slot = kNoDense;
+  if (DENSE && LOG2W >= 3 && tid < min(2 * kKwBatch, qb - qa))
+    pre_slot = A.dense_slot[A.q_kw[qa + tid]];
 
   // ---- reset this block's c-PQ ------------------------------------------
   // The query's k and bound and the range's first id live in S.gate from
@@ -861,8 +868,8 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
     // the tile prefix sums are not in use yet: room for the bitmap pointers
     const uint2** ptrs = reinterpret_cast<const uint2**>(
         (reinterpret_cast<uintptr_t>(tile_pre) + 7) & ~(uintptr_t)7);
-    const uint32_t nd = dense_phase<LOG2W>(A, g, qa, qb, bc, nwords, reinterpret_cast<uint32_t*>(seg),
-                                           ptrs, !gateless, S);
+    const uint32_t nd = dense_phase<LOG2W>(A, g, qa, qb, pre_slot, bc, nwords,
+                                           reinterpret_cast<uint32_t*>(seg), ptrs, !gateless, S);
     if (tid == 0) S.n_dense = nd;
   } else if (tid == 0) {
     S.n_dense = 0;
