@@ -559,7 +559,8 @@ __device__ __noinline__ void publish_seed(uint32_t* hh, uint32_t* seed,
     atomicAdd(&hh[at_f - 1], n_tie);
     added = 1;
   }
-  __threadfence();
+  // No fence: the barrier orders the block's additions before its reads, and
+  // a seed taken from any part of the histogram is still a valid one.
   if (!__syncthreads_or(added)) return;
   const uint32_t x = hist_kth(hh, B, k, scratch, *s_res);
   if (threadIdx.x == 0 && x) atomicMax(seed, x);
