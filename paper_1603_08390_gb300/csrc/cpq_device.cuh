@@ -538,15 +538,17 @@ __device__ __forceinline__ uint32_t hist_kth(const uint32_t* h, uint32_t B, uint
 // Adds the counts a finished range reports (cand[0..n_hi) and n_tie ties at
 // at_f - 1) that lie above the query's current seed to the query's histogram
 // hh, then raises the seed to the k-th largest count the histogram holds.
+// h0: the seed as read a little earlier; it only grows, so an early read
+// lets in some counts at or below the current seed, which are still reported
+// counts of distinct objects.
 // The histogram counts a subset of the reported objects, so that k-th
 // largest is still at most the query's k-th count; counts at or below the
 // current seed cannot raise it and are left out.  All threads of the block
 // call it.
-__device__ __noinline__ void publish_seed(uint32_t* hh, uint32_t* seed,
+__device__ __noinline__ void publish_seed(uint32_t* hh, uint32_t* seed, uint32_t h0,
                                           const unsigned long long* cand, uint32_t n_hi,
                                           uint32_t n_tie, uint32_t at_f, uint32_t B, uint32_t k,
                                           uint32_t* scratch, uint32_t* s_res) {
-  const uint32_t h0 = *(volatile uint32_t*)seed;
   int added = 0;
   for (uint32_t i = threadIdx.x; i < n_hi; i += blockDim.x) {
     const uint32_t c = dev::key_count(cand[i]);
@@ -627,6 +629,7 @@ struct BlockShared {
   uint32_t at0;       // AuditThreshold the range started with
   uint32_t gateless;  // count only, then select from the Bitmap Counter
   uint32_t tie_floor; // ties below it are left out of the read-out
+  uint32_t hint_now;  // the query's seed as the read-out began
   uint32_t next_run;  // next run of tiles to be claimed
   uint32_t n_dense;   // dense keywords whose bitmaps the range added
   uint32_t n_found;   // objects the dense phase found at or above AT
@@ -1058,6 +1061,9 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   const uint32_t kq = S.gate.kq, B = S.gate.B, obj_base = S.gate.obj_base;
   const uint32_t n_local = min(1u << A.block_shift, A.n_objects - obj_base);
   const uint32_t nwords_local = (n_local + PER - 1) / PER;
+  // the query's current seed, read by one thread while AT_f is settled
+  uint32_t hint_now = 0;
+  if (tid == 0 && A.at_hint) hint_now = vld(&A.at_hint[qi]);
   if (gateless) {
     // the k-th count of the range: largest x with #{count >= x} >= k
     const uint32_t t = kth_count<LOG2W>(bc, nwords_local, kq, scratch, S.scratch64);
@@ -1075,7 +1081,10 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
   // may be raising) is at most the query's k-th count, so ties below it
   // cannot reach the query's top-k.  One thread reads it: every thread must
   // take the same branch around the block-wide tie collection.
-  if (tid == 0) S.tie_floor = max(S.at0, A.at_hint ? vld(&A.at_hint[qi]) : 0u);
+  if (tid == 0) {
+    S.tie_floor = max(S.at0, hint_now);
+    S.hint_now = hint_now;
+  }
   __syncthreads();
   const uint32_t at_f = s_at;
   unsigned long long* out = A.cand + ((unsigned long long)qi * A.n_groups + g) * A.k;
@@ -1117,8 +1126,8 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
 
   if (A.chunk_at && tid == 0) A.chunk_at[(unsigned long long)qi * A.n_groups + g] = at_f;
   if (A.at_hint && A.hint_hist) {
-    publish_seed(A.hint_hist + (size_t)qi * A.hint_stride, &A.at_hint[qi], cand, n_hi, n_tie, at_f, B,
-                 kq, scratch, &S.kth);
+    publish_seed(A.hint_hist + (size_t)qi * A.hint_stride, &A.at_hint[qi], S.hint_now, cand, n_hi,
+                 n_tie, at_f, B, kq, scratch, &S.kth);
   } else if (A.at_hint && tid == 0 && at_f >= 2) {
     atomicMax(&A.at_hint[qi], at_f - 1);
   }
