@@ -1051,8 +1051,11 @@ __device__ __forceinline__ void cpq_item(const ScanArgs& A, uint32_t qi, uint32_
         t_end = tn_end;
       }
     };
+    // 16-bit counters always have headroom (count bounds are at most
+    // GENIE_MAX_BOUND), so their kernels carry no per-lane mode
+    static_assert(GENIE_MAX_BOUND < (1u << 15), "16-bit counters need lane headroom");
     if (gateless) tile_loop(GateMode<0>{});
-    else if (swar) tile_loop(GateMode<1>{});
+    else if (LOG2W == 4 || swar) tile_loop(GateMode<1>{});
     else tile_loop(GateMode<2>{});
     __syncthreads();
   }
