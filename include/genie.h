@@ -684,8 +684,12 @@ void genie_parts_destroy(genie_parts* parts);
  * the global ids id_base .. id_base + n - 1.  The index is not changed and
  * may be destroyed after the call.  Parts must be added in ascending,
  * disjoint id ranges and share one vocabulary; id_base + n must stay below
- * 2^32 - 1.  Synchronises `stream`.  Errors: INVALID_ARG (order, overlap,
- * vocabulary, id range), OUT_OF_MEMORY, CUDA.
+ * 2^32 - 1.  When the index's object ranges hold at most 2^16 ids
+ * (chunk_shift <= 16), the part keeps each id as its 16-bit place in its
+ * range, and the search rebuilds the ids on the device from the sublist map
+ * (half the List Array's host memory and copy bytes).  Synchronises `stream`.
+ * Errors: INVALID_ARG (order, overlap, vocabulary, id range), OUT_OF_MEMORY,
+ * CUDA.
  */
 genie_status genie_parts_add(genie_parts* parts, const genie_index* index, uint32_t id_base,
                              genie_stream stream);

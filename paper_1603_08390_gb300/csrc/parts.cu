@@ -13,6 +13,12 @@
 // is exact under (count desc, id asc): the batch's top-k is a subset of the
 // union of the parts' top-k lists, and parts come in ascending id order, so
 // ties at the k-th count are taken in ascending id.
+//
+// The List Array is most of a part's bytes, and the copy from host memory is
+// the leg's bound.  An id in range c is (c << chunk_shift) | place, and the
+// sublist map already says where range c starts in each list, so with
+// chunk_shift <= 16 a part keeps only the 16-bit places in host memory; the
+// device rebuilds the ids from them before the part's search.
 #include <algorithm>
 #include <vector>
 
@@ -28,9 +34,80 @@ struct HostPart {
   uint32_t n_objects = 0, max_object_len = 0, chunk_shift = 0, n_chunks = 0;
   uint64_t nnz = 0, post_len = 0, chunk_len = 0;
   uint64_t* kw_off = nullptr;    // pinned host copies of the index arrays
-  uint32_t* post_ids = nullptr;
+  uint32_t* post_ids = nullptr;  // NULL when the part keeps 16-bit places
+  uint16_t* post16 = nullptr;    // the ids' places in their ranges (chunk_shift <= 16)
   uint32_t* chunk_pos = nullptr;
+  uint64_t post_bytes() const { return post_len * (post16 ? 2 : 4); }
 };
+
+// ids -> their places in their object ranges (the low chunk_shift bits)
+__global__ void narrow_ids_kernel(const uint32_t* __restrict__ ids, uint64_t n, uint32_t mask,
+                                  uint16_t* __restrict__ out) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = (uint16_t)(ids[i] & mask);
+}
+
+// places -> ids.  The List Array is cut into segments of kWidenSeg
+// positions, one block each; lists can be long (one LSH bucket may hold a
+// large share of the objects), so the work follows positions, not keywords.
+constexpr uint32_t kWidenThreads = 256, kWidenPer = 8, kWidenSeg = kWidenThreads * kWidenPer;
+
+// seg_kw[s] = the keyword whose list holds position min(s * kWidenSeg, nnz - 1),
+// for s = 0 .. n_seg: the largest keyword whose list starts at or before it.
+__global__ void segment_keywords_kernel(const uint64_t* __restrict__ kw_off, uint32_t vocab,
+                                        uint64_t nnz, uint32_t n_seg, uint32_t* __restrict__ seg_kw) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s <= n_seg; s += gridDim.x * blockDim.x) {
+    const uint64_t pos = min((uint64_t)s * kWidenSeg, nnz - 1);
+    uint32_t kw = 0;  // kw_off[kw] <= pos, the answer in [kw, kw + n)
+    for (uint32_t n = vocab; n > 1;) {
+      const uint32_t half = n >> 1;
+      if (kw_off[kw + half] <= pos) kw += half;
+      n -= half;
+    }
+    seg_kw[s] = kw;
+  }
+}
+
+// Each thread takes kWidenPer positions of its block's segment and finds, for
+// each, the keyword (between the segment's first and last keyword) and then
+// the range (from the keyword's row of the sublist map, whose entry c is the
+// first position of range c) by binary searches of a fixed number of steps,
+// the positions' searches interleaved so that their loads overlap.
+__global__ void __launch_bounds__(kWidenThreads)
+    widen_ids_kernel(const uint64_t* __restrict__ kw_off, const uint32_t* __restrict__ chunk_pos,
+                     uint32_t nch, uint32_t shift, uint64_t nnz, const uint32_t* __restrict__ seg_kw,
+                     const uint16_t* __restrict__ in, uint32_t* __restrict__ ids) {
+  const uint64_t s0 = (uint64_t)blockIdx.x * kWidenSeg + threadIdx.x;
+  const uint32_t lo = seg_kw[blockIdx.x], hi = seg_kw[blockIdx.x + 1];
+  uint64_t pc[kWidenPer];  // the position, clamped into the List Array
+  uint32_t place[kWidenPer], kw[kWidenPer], c[kWidenPer];
+#pragma unroll
+  for (uint32_t j = 0; j < kWidenPer; ++j) {
+    pc[j] = min(s0 + j * kWidenThreads, nnz - 1);
+    place[j] = in[pc[j]];
+    kw[j] = lo;
+    c[j] = 0;
+  }
+  for (uint32_t n = hi - lo + 1; n > 1;) {  // kw_off[kw[j]] <= pc[j]; the answer in [kw[j], kw[j] + n)
+    const uint32_t half = n >> 1;
+#pragma unroll
+    for (uint32_t j = 0; j < kWidenPer; ++j) kw[j] += kw_off[kw[j] + half] <= pc[j] ? half : 0u;
+    n -= half;
+  }
+#pragma unroll
+  for (uint32_t j = 0; j < kWidenPer; ++j) pc[j] -= kw_off[kw[j]];  // the position in its list
+  for (uint32_t n = nch; n > 1;) {  // row[c[j]] <= pc[j]; the answer in [c[j], c[j] + n)
+    const uint32_t half = n >> 1;
+#pragma unroll
+    for (uint32_t j = 0; j < kWidenPer; ++j)
+      c[j] += chunk_pos[(uint64_t)kw[j] * (nch + 1) + c[j] + half] <= pc[j] ? half : 0u;
+    n -= half;
+  }
+#pragma unroll
+  for (uint32_t j = 0; j < kWidenPer; ++j)
+    if (s0 + j * kWidenThreads < nnz) ids[s0 + j * kWidenThreads] = (c[j] << shift) | place[j];
+}
 
 // part outputs [P][Q][k] -> result keys [Q][P][k] with global ids (0 past n_valid)
 __global__ void part_keys_kernel(const uint32_t* __restrict__ ids, const uint32_t* __restrict__ counts,
@@ -70,6 +147,8 @@ struct genie_parts {
   std::vector<HostPart> parts;
   // two device slots, each a complete index view sized for the largest part
   genie_index slot[2];
+  uint16_t* stage16[2] = {nullptr, nullptr};  // a part's 16-bit places on their way in
+  uint32_t* seg_kw = nullptr;                 // the first keyword of each segment (widening)
   uint64_t slot_post_cap = 0, slot_chunk_cap = 0;
   cudaStream_t copy = nullptr;
   cudaEvent_t copied[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
@@ -86,17 +165,27 @@ void free_slots(genie_parts* ps) {
     s.post_ids = nullptr;
     s.chunk_pos = nullptr;
   }
+  for (uint16_t*& b : ps->stage16) {
+    cudaFree(b);
+    b = nullptr;
+  }
+  cudaFree(ps->seg_kw);
+  ps->seg_kw = nullptr;
   ps->slot_post_cap = ps->slot_chunk_cap = 0;
 }
 
 // device slots large enough for every part
 cudaError_t ensure_slots(genie_parts* ps) {
   uint64_t post = 0, chunk = 0;
+  bool narrow = false;
   for (const HostPart& h : ps->parts) {
     post = std::max(post, h.post_len);
     chunk = std::max(chunk, h.chunk_len);
+    narrow |= h.post16 != nullptr;
   }
-  if (post <= ps->slot_post_cap && chunk <= ps->slot_chunk_cap && ps->slot[0].kw_off) return cudaSuccess;
+  if (post <= ps->slot_post_cap && chunk <= ps->slot_chunk_cap && ps->slot[0].kw_off &&
+      (!narrow || ps->stage16[0]))
+    return cudaSuccess;
   free_slots(ps);
   cudaError_t e = cudaSuccess;
   for (genie_index& s : ps->slot) {
@@ -106,6 +195,9 @@ cudaError_t ensure_slots(genie_parts* ps) {
     s.device = ps->device;
     s.vocab = ps->vocab;
   }
+  for (uint16_t*& b : ps->stage16)
+    if (e == cudaSuccess && narrow) e = cudaMalloc(&b, post * 2);
+  if (e == cudaSuccess && narrow) e = cudaMalloc(&ps->seg_kw, (post / kWidenSeg + 2) * 4);
   if (e != cudaSuccess) {
     free_slots(ps);
     return e;
@@ -141,6 +233,7 @@ extern "C" void genie_parts_destroy(genie_parts* ps) {
   for (HostPart& h : ps->parts) {
     cudaFreeHost(h.kw_off);
     cudaFreeHost(h.post_ids);
+    cudaFreeHost(h.post16);
     cudaFreeHost(h.chunk_pos);
   }
   free_slots(ps);
@@ -173,20 +266,37 @@ extern "C" genie_status genie_parts_add(genie_parts* ps, const genie_index* inde
   h.post_len = ((index->nnz + 3) & ~3ull) + 4;  // the padded List Array
   h.chunk_len = (uint64_t)index->vocab * (index->n_chunks + 1);
   cudaStream_t s = as_stream(stream);
+  const bool narrow = index->chunk_shift <= 16;  // the places fit in 16 bits
+  uint16_t* d16 = nullptr;
   cudaError_t e = cudaMallocHost(&h.kw_off, ((uint64_t)index->vocab + 1) * 8);
-  if (e == cudaSuccess) e = cudaMallocHost(&h.post_ids, h.post_len * 4);
+  if (e == cudaSuccess && narrow) e = cudaMallocHost(&h.post16, h.post_len * 2);
+  if (e == cudaSuccess && !narrow) e = cudaMallocHost(&h.post_ids, h.post_len * 4);
   if (e == cudaSuccess) e = cudaMallocHost(&h.chunk_pos, h.chunk_len * 4);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h.kw_off, index->kw_off, ((uint64_t)index->vocab + 1) * 8,
                         cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && narrow) {
+    e = cudaMallocAsync((void**)&d16, h.post_len * 2, s);
+    if (e == cudaSuccess) {
+      narrow_ids_kernel<<<grid_for(h.post_len, 256), 256, 0, s>>>(
+          index->post_ids, h.post_len, (1u << index->chunk_shift) - 1u, d16);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.post16, d16, h.post_len * 2, cudaMemcpyDeviceToHost, s);
+    if (d16) {
+      cudaError_t f = cudaFreeAsync(d16, s);
+      if (e == cudaSuccess) e = f;
+    }
+  } else if (e == cudaSuccess) {
     e = cudaMemcpyAsync(h.post_ids, index->post_ids, h.post_len * 4, cudaMemcpyDeviceToHost, s);
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h.chunk_pos, index->chunk_pos, h.chunk_len * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     cudaFreeHost(h.kw_off);
     cudaFreeHost(h.post_ids);
+    cudaFreeHost(h.post16);
     cudaFreeHost(h.chunk_pos);
     return fail_cuda(e, "genie_parts_add");
   }
@@ -203,7 +313,7 @@ extern "C" genie_status genie_parts_get_info(const genie_parts* ps, genie_parts_
   out->host_bytes = 0;
   out->max_part_bytes = 0;
   for (const HostPart& h : ps->parts) {
-    const uint64_t b = ((uint64_t)ps->vocab + 1) * 8 + h.post_len * 4 + h.chunk_len * 4;
+    const uint64_t b = ((uint64_t)ps->vocab + 1) * 8 + h.post_bytes() + h.chunk_len * 4;
     out->host_bytes += b;
     out->max_part_bytes = std::max(out->max_part_bytes, b);
   }
@@ -247,7 +357,9 @@ extern "C" genie_status genie_parts_search(genie_parts* ps, const uint32_t* d_q_
     if (r == cudaSuccess)
       r = cudaMemcpyAsync(sl.kw_off, h.kw_off, ((uint64_t)ps->vocab + 1) * 8, cudaMemcpyHostToDevice,
                           ps->copy);
-    if (r == cudaSuccess)
+    if (r == cudaSuccess && h.post16)
+      r = cudaMemcpyAsync(ps->stage16[p & 1], h.post16, h.post_len * 2, cudaMemcpyHostToDevice, ps->copy);
+    else if (r == cudaSuccess)
       r = cudaMemcpyAsync(sl.post_ids, h.post_ids, h.post_len * 4, cudaMemcpyHostToDevice, ps->copy);
     if (r == cudaSuccess)
       r = cudaMemcpyAsync(sl.chunk_pos, h.chunk_pos, h.chunk_len * 4, cudaMemcpyHostToDevice, ps->copy);
@@ -264,6 +376,22 @@ extern "C" genie_status genie_parts_search(genie_parts* ps, const uint32_t* d_q_
     if (e != cudaSuccess) break;
     const HostPart& h = ps->parts[p];
     genie_index& sl = ps->slot[p & 1];
+    if (h.post16) {
+      // ids from their places (zero padding after the lists).  On `s`, not on
+      // the copy stream, so that the next part's copy never waits for SMs
+      // that this part's search holds.
+      const uint32_t n_seg = (uint32_t)((h.nnz + kWidenSeg - 1) / kWidenSeg);
+      if (n_seg) {
+        segment_keywords_kernel<<<grid_for(n_seg + 1ull, 256), 256, 0, s>>>(sl.kw_off, ps->vocab, h.nnz,
+                                                                          n_seg, ps->seg_kw);
+        widen_ids_kernel<<<n_seg, kWidenThreads, 0, s>>>(sl.kw_off, sl.chunk_pos, h.n_chunks,
+                                                         h.chunk_shift, h.nnz, ps->seg_kw,
+                                                         ps->stage16[p & 1], sl.post_ids);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaMemsetAsync(sl.post_ids + h.nnz, 0, (h.post_len - h.nnz) * 4, s);
+      if (e != cudaSuccess) break;
+    }
     sl.n_objects = h.n_objects;
     sl.nnz = h.nnz;
     sl.max_object_len = h.max_object_len;

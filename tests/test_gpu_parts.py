@@ -96,3 +96,29 @@ def test_part_store_inputs_are_checked():
     for x in (a, b, parts):
         x.close()
     del off
+
+
+@pytest.mark.parametrize("chunk_shift", [12, 16, 17])
+def test_parts_carry_16_bit_places_or_full_ids(chunk_shift):
+    """With object ranges of at most 2^16 ids a part keeps each id's place in
+    its range (16 bits) in host memory and the device rebuilds the ids from
+    the sublist map; wider ranges keep the full ids.  Both equal the oracle.
+    At 2^12 ids per range the middle part spans 37 ranges, more than one
+    warp-wide read of a keyword's row of the sublist map."""
+    w = synth.sets(300_000, (16, 64), 1 << 16, 40, (8, 100), 10, config=53)
+    ranges = [(0, 100_000), (100_000, 250_001), (250_001, 300_000)]
+    parts = runner.build_parts(w, ranges, chunk_shift=chunk_shift)
+    got = runner.search_parts(parts, w, 10).host()
+    torch.cuda.synchronize()
+    _check(got, oracle.topk(w))
+    again = runner.search_parts(parts, w, 10).host()   # the staging buffers are reused
+    for key in got:
+        assert np.array_equal(got[key], again[key]), key
+    nnz = int(w.obj_off[-1])
+    pad = sum(((int(w.obj_off[b]) - int(w.obj_off[a]) + 3) & ~3) + 4 for a, b in ranges)
+    other = parts.info.host_bytes - (pad - nnz) * (2 if chunk_shift <= 16 else 4)
+    post = nnz * (2 if chunk_shift <= 16 else 4)
+    # kw_off and the sublist map are the rest of the pinned bytes
+    n_ch = sum(-(-(b - a) >> chunk_shift) + 1 for a, b in ranges)
+    assert other - post == 3 * (w.vocab + 1) * 8 + w.vocab * n_ch * 4
+    parts.close()
