@@ -852,6 +852,7 @@ def leg_parts(args, keep):
                                   "parts of 1,000,000 in pinned host memory; 1024 queries, k=100",
                       "n_objects": N, "n_queries": Q, "k": k, "parts": P},
            "value": Q * steps / (p_ms / 1e3), "ms_per_step": p_ms / steps,
+           # with more than two parts every call copies each part once
            "h2d_bytes_per_step": int(info.host_bytes),
            "h2d_gb_per_s": info.host_bytes * steps / (p_ms / 1e3) / 1e9,
            "device_resident": {"value": Q * steps / (d_ms / 1e3), "ms_per_step": d_ms / steps,

@@ -701,10 +701,15 @@ genie_status genie_parts_get_info(const genie_parts* parts, genie_parts_info* ou
  *   d_q_off [n_queries+1], d_q_kw: keyword queries, as for genie_make_queries
  *                (device; read once per part).
  *   k, d_k, d_ids, d_counts, d_n_valid: as for genie_search; ids are global.
- * Each part is loaded into a device slot (the first on the call, the next
- * ones overlapped with the search of the one before), its queries are
- * compiled and searched as by genie_make_queries + genie_search, and the
- * per-part lists are merged on the device.  Results equal those of one index
+ * Each part is loaded into a device slot (the next one overlapped with the
+ * search of the one before), its queries are compiled and searched as by
+ * genie_make_queries + genie_search, and the per-part lists are merged on
+ * the device.  Part p goes to slot p mod 2, and a part still in its slot
+ * from the call before is not copied again: with one or two parts, only the
+ * first call copies.  With an even number of parts, a call loads part 0 into
+ * its slot while it searches the last part, so the next call starts without
+ * a copy; each call still copies every part once when there are more than
+ * two.  Results equal those of one index
  * over all objects: ids in (count desc, id asc) order, unused slots id
  * 0xFFFFFFFF and count 0.  Synchronises `stream` once per part (the query
  * compile) and waits for the copy stream before it returns.  Calls on one

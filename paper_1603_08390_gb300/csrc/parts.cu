@@ -149,6 +149,8 @@ struct genie_parts {
   genie_index slot[2];
   uint16_t* stage16[2] = {nullptr, nullptr};  // a part's 16-bit places on their way in
   uint32_t* seg_kw = nullptr;                 // the first keyword of each segment (widening)
+  int64_t slot_part[2] = {-1, -1};            // the part a slot holds (-1: none)
+  bool slot_wide[2] = {false, false};         // its ids are rebuilt from the 16-bit places
   uint64_t slot_post_cap = 0, slot_chunk_cap = 0;
   cudaStream_t copy = nullptr;
   cudaEvent_t copied[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
@@ -171,6 +173,7 @@ void free_slots(genie_parts* ps) {
   }
   cudaFree(ps->seg_kw);
   ps->seg_kw = nullptr;
+  ps->slot_part[0] = ps->slot_part[1] = -1;
   ps->slot_post_cap = ps->slot_chunk_cap = 0;
 }
 
@@ -353,6 +356,9 @@ extern "C" genie_status genie_parts_search(genie_parts* ps, const uint32_t* d_q_
   auto load = [&](uint32_t p) -> cudaError_t {
     const HostPart& h = ps->parts[p];
     genie_index& sl = ps->slot[p & 1];
+    if (ps->slot_part[p & 1] == (int64_t)p) return cudaSuccess;  // still there from the call before
+    ps->slot_part[p & 1] = p;
+    ps->slot_wide[p & 1] = false;
     cudaError_t r = cudaStreamWaitEvent(ps->copy, ps->used[p & 1], 0);
     if (r == cudaSuccess)
       r = cudaMemcpyAsync(sl.kw_off, h.kw_off, ((uint64_t)ps->vocab + 1) * 8, cudaMemcpyHostToDevice,
@@ -371,12 +377,15 @@ extern "C" genie_status genie_parts_search(genie_parts* ps, const uint32_t* d_q_
   if (e == cudaSuccess) e = load(0);
   for (uint32_t p = 0; p < P && e == cudaSuccess && st == GENIE_OK; ++p) {
     if (p + 1 < P) e = load(p + 1);  // overlaps the search of part p
+    // With an even number of parts, part 0's slot is free while the last one
+    // is searched: load part 0 there for the next call.
+    else if (P % 2 == 0) e = load(0);
     if (e != cudaSuccess) break;
     e = cudaStreamWaitEvent(s, ps->copied[p & 1], 0);
     if (e != cudaSuccess) break;
     const HostPart& h = ps->parts[p];
     genie_index& sl = ps->slot[p & 1];
-    if (h.post16) {
+    if (h.post16 && !ps->slot_wide[p & 1]) {
       // ids from their places (zero padding after the lists).  On `s`, not on
       // the copy stream, so that the next part's copy never waits for SMs
       // that this part's search holds.
@@ -391,6 +400,7 @@ extern "C" genie_status genie_parts_search(genie_parts* ps, const uint32_t* d_q_
       }
       if (e == cudaSuccess) e = cudaMemsetAsync(sl.post_ids + h.nnz, 0, (h.post_len - h.nnz) * 4, s);
       if (e != cudaSuccess) break;
+      ps->slot_wide[p & 1] = true;
     }
     sl.n_objects = h.n_objects;
     sl.nnz = h.nnz;
@@ -435,6 +445,8 @@ extern "C" genie_status genie_parts_search(genie_parts* ps, const uint32_t* d_q_
   // the copy stream must not write a slot after this call returns
   cudaError_t e2 = cudaStreamSynchronize(ps->copy);
   cudaFreeAsync(base, s);
+  if (st != GENIE_OK || e != cudaSuccess || e2 != cudaSuccess)
+    ps->slot_part[0] = ps->slot_part[1] = -1;  // a slot may hold part of a part
   if (st != GENIE_OK) return st;
   if (e == cudaSuccess) e = e2;
   if (e != cudaSuccess) return fail_cuda(e, "genie_parts_search");

@@ -122,3 +122,32 @@ def test_parts_carry_16_bit_places_or_full_ids(chunk_shift):
     n_ch = sum(-(-(b - a) >> chunk_shift) + 1 for a, b in ranges)
     assert other - post == 3 * (w.vocab + 1) * 8 + w.vocab * n_ch * 4
     parts.close()
+
+
+@pytest.mark.parametrize("n_parts", [2, 4])
+def test_parts_kept_in_their_slots_between_calls(n_parts):
+    """Parts still in a device slot are not copied again, and with an even
+    number of parts the last part's search overlaps the copy of part 0 for
+    the next call.  Three calls in a row (k = 10, per-query k, k = 1), then a
+    part larger than the others appended (the slots grow and are refilled)
+    and two more calls: all equal the oracle."""
+    w = synth.lsh(80_000, 40, 30, config=54)
+    N, half = w.n_objects, w.n_objects // 2
+    cuts = [i * half // n_parts for i in range(n_parts + 1)]
+    parts = runner.build_parts(w, list(zip(cuts[:-1], cuts[1:])))
+    ks = np.random.default_rng(5).integers(1, 31, w.n_queries).astype(np.uint32)
+    for k in (10, ks, 1):
+        got = runner.search_parts(parts, w, k).host()
+        torch.cuda.synchronize()
+        _check(got, oracle.topk(w, k=k, obj_range=(0, half)))
+    off = w.obj_off.astype(np.int64)
+    sub_off = (off[half:] - off[half]).astype(np.uint32)
+    idx = genie.genie_build_index(runner.to_dev(sub_off), runner.to_dev(w.obj_kw[off[half]:]),
+                                  N - half, w.vocab, 0, None)
+    parts.add(idx, half)
+    idx.close()
+    for _ in range(2):
+        got = runner.search_parts(parts, w, 10).host()
+        torch.cuda.synchronize()
+        _check(got, oracle.topk(w, k=10))
+    parts.close()
