@@ -69,16 +69,25 @@ __global__ void segment_keywords_kernel(const uint64_t* __restrict__ kw_off, uin
   }
 }
 
-// Each thread takes kWidenPer positions of its block's segment and finds, for
-// each, the keyword (between the segment's first and last keyword) and then
-// the range (from the keyword's row of the sublist map, whose entry c is the
-// first position of range c) by binary searches of a fixed number of steps,
-// the positions' searches interleaved so that their loads overlap.
+// Each thread takes kWidenPer positions of its block's segment.  The block
+// lists the start of every sublist of the segment's keywords (lo .. hi, each
+// with nch ranges), as an offset from the segment's first position clamped to
+// [0, kWidenSeg], in shared memory: the starts do not decrease in (keyword,
+// range) order, and a position's sublist is the last one that starts at or
+// before it.  One coalesced read fills the table and each position searches it
+// on chip.  A segment with more than kWidenFlat sublists (many short lists)
+// searches the keyword and then the range in global memory instead: binary
+// searches with a fixed number of steps, the positions' searches interleaved
+// so that their loads overlap.
+constexpr uint32_t kWidenFlat = 4096;
+
 __global__ void __launch_bounds__(kWidenThreads)
     widen_ids_kernel(const uint64_t* __restrict__ kw_off, const uint32_t* __restrict__ chunk_pos,
                      uint32_t nch, uint32_t shift, uint64_t nnz, const uint32_t* __restrict__ seg_kw,
                      const uint16_t* __restrict__ in, uint32_t* __restrict__ ids) {
-  const uint64_t s0 = (uint64_t)blockIdx.x * kWidenSeg + threadIdx.x;
+  __shared__ uint32_t start[kWidenFlat];
+  const uint64_t seg0 = (uint64_t)blockIdx.x * kWidenSeg;
+  const uint64_t s0 = seg0 + threadIdx.x;
   const uint32_t lo = seg_kw[blockIdx.x], hi = seg_kw[blockIdx.x + 1];
   uint64_t pc[kWidenPer];  // the position, clamped into the List Array
   uint32_t place[kWidenPer], kw[kWidenPer], c[kWidenPer];
@@ -88,6 +97,31 @@ __global__ void __launch_bounds__(kWidenThreads)
     place[j] = in[pc[j]];
     kw[j] = lo;
     c[j] = 0;
+  }
+  const uint64_t n_flat = (uint64_t)(hi - lo + 1) * nch;  // the same for the whole block
+  if (n_flat <= kWidenFlat) {
+    for (uint32_t t = threadIdx.x; t < n_flat; t += kWidenThreads) {
+      const uint32_t v = lo + t / nch, r = t % nch;
+      const uint64_t a = kw_off[v] + chunk_pos[(uint64_t)v * (nch + 1) + r];
+      start[t] = (uint32_t)(a <= seg0 ? 0 : min(a - seg0, (uint64_t)kWidenSeg));
+    }
+    __syncthreads();
+    uint32_t f[kWidenPer], rel[kWidenPer];
+#pragma unroll
+    for (uint32_t j = 0; j < kWidenPer; ++j) {
+      f[j] = 0;  // start[f[j]] <= rel[j]; the answer in [f[j], f[j] + n)
+      rel[j] = (uint32_t)(pc[j] - seg0);
+    }
+    for (uint32_t n = (uint32_t)n_flat; n > 1;) {
+      const uint32_t half = n >> 1;
+#pragma unroll
+      for (uint32_t j = 0; j < kWidenPer; ++j) f[j] += start[f[j] + half] <= rel[j] ? half : 0u;
+      n -= half;
+    }
+#pragma unroll
+    for (uint32_t j = 0; j < kWidenPer; ++j)
+      if (s0 + j * kWidenThreads < nnz) ids[s0 + j * kWidenThreads] = ((f[j] % nch) << shift) | place[j];
+    return;
   }
   for (uint32_t n = hi - lo + 1; n > 1;) {  // kw_off[kw[j]] <= pc[j]; the answer in [kw[j], kw[j] + n)
     const uint32_t half = n >> 1;
