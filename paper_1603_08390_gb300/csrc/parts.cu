@@ -14,9 +14,9 @@
 // union of the parts' top-k lists, and parts come in ascending id order, so
 // ties at the k-th count are taken in ascending id.
 //
-// The List Array is most of a part's bytes, and the copy from host memory is
-// the leg's bound.  An id in range c is (c << chunk_shift) | place, and the
-// sublist map already says where range c starts in each list, so with
+// The List Array is most of a part's bytes, and with 32-bit ids its copy from
+// host memory bounds a batch.  An id in range c is (c << chunk_shift) | place,
+// and the sublist map already says where range c starts in each list, so with
 // chunk_shift <= 16 a part keeps only the 16-bit places in host memory; the
 // device rebuilds the ids from them before the part's search.
 #include <algorithm>
@@ -49,8 +49,8 @@ __global__ void narrow_ids_kernel(const uint32_t* __restrict__ ids, uint64_t n, 
 }
 
 // places -> ids.  The List Array is cut into segments of kWidenSeg
-// positions, one block each; lists can be long (one LSH bucket may hold a
-// large share of the objects), so the work follows positions, not keywords.
+// positions, one block each: list lengths range from one posting to a large
+// share of the part, so the work follows positions, not keywords.
 constexpr uint32_t kWidenThreads = 256, kWidenPer = 8, kWidenSeg = kWidenThreads * kWidenPer;
 
 // seg_kw[s] = the keyword whose list holds position min(s * kWidenSeg, nnz - 1),
